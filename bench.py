@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Benchmark: TFT polynomial product throughput on one GB300.
+
+Workload (one step = one pass of the whole hot path): the TFT product of
+two operands of lengths 3,000,000 and 5,000,001 over Z/(2^64 - 2^32 + 1),
+uniform residues from seed 2 (r = 8,000,000): column TFTs of both operands,
+fused row pass (forward row transforms of both, pointwise product, inverse
+row transform), inverse column passes and the ragged last row.  Inputs are
+resident in HBM when the timed region starts; L2 is flushed between timed
+steps by writing a 256 MiB buffer outside the per-step CUDA events.
+
+Also reported: the same metric end to end through the host-buffer C entry
+point (pinned host inputs, H2D + product + D2H per step); the single
+forward and inverse TFT of length 2^24 + 2^20 + 12345 (k = 25); per-kernel
+CUDA-event durations from the library's profiler; the roofline of the
+dominant kernel; the oracle on the host cores as the CPU baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs one independent replica per GPU (the product does not shard;
+no collective on the data path) and reports the aggregate throughput.
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("TFT polymul Mcoeff/s & % HBM roofline, bit-exact; "
+          "served p50/p99 vs plain")
+WORKLOAD = "polymul_goldilocks_3000000x5000001"
+NA, NB = 3_000_000, 5_000_001
+R_PROD = NA + NB - 1
+TFT_N = 2**24 + 2**20 + 12345
+P_GOLD = 2**64 - 2**32 + 1
+
+# Integer-multiply roofline (sm_103a unit counts and clock):
+# 152 SMs x 64 lanes of 32-bit IMAD per SM per clock x 2.07 GHz, and a
+# 64 x 64 -> 128-bit product needs 4 32 x 32 -> 64-bit partial products.
+SMS = 152
+IMAD_LANES_PER_SM_CLK = 64
+SM_MAX_GHZ = 2.07
+MUL32_PER_MODMUL_GOLD = 4
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the single-transform and e2e legs")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic work (for the roofline)
+# ---------------------------------------------------------------------------
+def tree_level_butterflies(n):
+    """Butterflies of the TFT tree of length n per level r (stride 2^r):
+    sum over the nodes (q, r), q < 2^r, of floor(len(q, r) / 2) with
+    len(q, r) = ceil((n - q) / 2^r) (Section 3).  These are the multiplies
+    Algorithm 1 performs besides its corrections."""
+    out = []
+    r = 0
+    while (1 << r) < n:
+        full, rem = divmod(n, 1 << r)
+        out.append(rem * ((full + 1) // 2) + ((1 << r) - rem) * (full // 2))
+        r += 1
+    return out
+
+
+def kernel_modmuls(plan, r_len):
+    """Algorithmic modular multiplies per launch of each kernel of the TFT
+    product of length r_len under ``plan``: levels below lr belong to the
+    row pass, levels from lr up to the column passes.  The fused row pass
+    runs the row levels of three transforms plus r pointwise products."""
+    bf = tree_level_butterflies(r_len)
+    lr = plan["lr"]
+    rows = sum(bf[:lr])
+    cols = sum(bf[lr:])
+    return {"k_col_fwd": cols, "k_row_mul": 3 * rows + r_len,
+            "k_col_inv": cols / 2, "k_lastrow_inv": 0}
+
+
+def aggregate(total_ms, units, world):
+    """Max of the per-rank timed totals and the units all ranks processed.
+    (Each rank passes its own numbers; with world > 1 torch.distributed is
+    initialised.)"""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_ms)], dtype=torch.float64,
+                         device="cuda" if dist.get_backend() == "nccl"
+                         else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([float(units)], dtype=torch.float64, device=t.device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        return float(t.item()), float(u.item())
+    return float(total_ms), float(units)
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, one product per host thread
+# ---------------------------------------------------------------------------
+def oracle_polymul_sample(scale=0.125, threads=None):
+    """Time the C oracle's TFT product (Algorithm 1 twice, pointwise,
+    Algorithm 2) on a proportionally scaled instance of the workload, one
+    product per thread.  Returns (Mcoeff/s, cores, description)."""
+    from oracle import native as NV
+    from workloads import config3_inputs
+    NV.build()
+    a, b = config3_inputs(scale=scale)
+    a = a.astype("uint64")
+    b = b.astype("uint64")
+    r = a.size + b.size - 1
+    threads = threads or min(os.cpu_count() or 1, 16)
+    errs = []
+
+    def one():
+        try:
+            NV.tft_polymul(2, a, b)
+        except Exception as e:  # pragma: no cover
+            errs.append(e)
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=one) for _ in range(threads)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    dt = time.perf_counter() - t0
+    if errs:
+        raise errs[0]
+    desc = (f"oracle C TFT product (Algorithm 1 x2, pointwise, Algorithm 2) "
+            f"on the {a.size} x {b.size} instance of the same workload "
+            f"(scale {scale}), one product per thread on {threads} threads")
+    return threads * r / dt / 1e6, threads, desc, dt
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    steps, warmup = max(1, args.steps), max(0, args.warmup)
+    for _ in range(warmup):
+        oracle_polymul_sample(scale=1 / 16)
+    vals, cores, desc, total = [], 0, "", 0.0
+    for _ in range(steps):
+        v, cores, desc, dt = oracle_polymul_sample(scale=1 / 16)
+        vals.append(v)
+        total += dt
+    value = statistics.mean(vals)
+    line = {"metric": METRIC, "value": value, "unit": "Mcoeff/s",
+            "n_gpus": args.gpus, "steps": steps, "warmup": warmup,
+            "ms_per_step": 1000 * total / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic: uniform residues mod p, seed 2",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample_scale": 1 / 16},
+            "cpu_baseline": {"value": value, "unit": "Mcoeff/s",
+                             "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "Mcoeff/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1001_5272_gb300 import tft
+    from workloads import config2_input, config3_inputs
+
+    world = env_int("WORLD_SIZE", 1)
+    rank = env_int("RANK", 0)
+    local = env_int("LOCAL_RANK", 0)
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    steps, warmup = max(1, args.steps), max(3, args.warmup)
+
+    a_np, b_np = config3_inputs()
+    a_pin = torch.from_numpy(a_np.view(np.int64)).pin_memory()
+    b_pin = torch.from_numpy(b_np.view(np.int64)).pin_memory()
+    a = a_pin.to(dev, non_blocking=True)
+    b = b_pin.to(dev, non_blocking=True)
+    out = torch.empty(R_PROD, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    ctx = tft.Context(2, dev, max_len=max(R_PROD, TFT_N),
+                      host_staging=not args.no_extra)
+    stream = torch.cuda.current_stream()
+    plan = tft.tft_describe_plan(2, R_PROD)
+
+    for _ in range(warmup):
+        tft.tft_polymul(ctx, a, b, out)
+    torch.cuda.synchronize()
+
+    # ---- timed region -----------------------------------------------------
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    sampler = ClockSampler(dev)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    tft.tft_profile_enable(ctx, True)
+    launches0 = tft.tft_launch_count(ctx)
+    wall0 = time.perf_counter()
+    for i in range(steps):
+        flush.zero_()
+        starts[i].record(stream)
+        tft.tft_polymul(ctx, a, b, out, stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    launches = tft.tft_launch_count(ctx) - launches0
+    prof = tft.tft_profile_read(ctx)
+    tft.tft_profile_enable(ctx, False)
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms, units = aggregate(sum(step_ms), steps * R_PROD, world)
+    value = units / (total_ms / 1e3) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel ---------------------------------
+    kernels = {k: {"ms_total": ms, "launches": n, "ms_per_launch": ms / n,
+                   "share": None}
+               for k, (ms, n) in prof.items()}
+    ksum = sum(v["ms_total"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["ms_total"] / ksum
+    dom = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    t_launch = kernels[dom]["ms_per_launch"] / 1e3
+    work = kernel_modmuls(plan, R_PROD)
+    mm = work.get(dom)
+    peak = SMS * IMAD_LANES_PER_SM_CLK * SM_MAX_GHZ * 1e9 / 1e12
+    achieved = (mm * MUL32_PER_MODMUL_GOLD / t_launch / 1e12
+                if mm else None)
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved,
+            "peak": peak, "unit": "Tmul32/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": None,
+            "work_per_launch": {"modmuls": mm,
+                                "mul32_per_modmul": MUL32_PER_MODMUL_GOLD},
+            "peak_source": "derived: 152 SMs x 64 IMAD lanes/clk x 2.07 GHz "
+                           "(unit counts and max clock)"}
+    # HBM view of the whole step for context
+    alg_bytes = (NA + NB + R_PROD) * 8
+    hbm_frac = None
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        hbm_peak = float(peaks["hbm_gbs"])
+        hbm_src = "measured"
+    except Exception:
+        hbm_peak, hbm_src = 6800.0, "fallback"
+    step_s = statistics.mean(step_ms) / 1e3
+    hbm_frac = alg_bytes / step_s / 1e9 / hbm_peak
+
+    # ---- single forward / inverse TFT (n = 2^24 + 2^20 + 12345) ----------
+    extra = {}
+    e2e = None
+    if not args.no_extra:
+        x_np = config2_input()
+        x = torch.from_numpy(x_np.view(np.int64)).to(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for _ in range(2):
+            tft.tft_forward(ctx, x, 25)
+            tft.tft_inverse(ctx, x, 25)
+        fwd_ms, inv_ms = [], []
+        for _ in range(max(3, steps // 2)):
+            flush.zero_()
+            ev[0].record(stream)
+            tft.tft_forward(ctx, x, 25, stream)
+            ev[1].record(stream)
+            flush.zero_()
+            ev[2].record(stream)
+            tft.tft_inverse(ctx, x, 25, stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            fwd_ms.append(ev[0].elapsed_time(ev[1]))
+            inv_ms.append(ev[2].elapsed_time(ev[3]))
+        ok = bool(torch.equal(x.cpu(), torch.from_numpy(x_np.view(np.int64))))
+        inplace_b, padded_b = tft.tft_footprint(2, TFT_N, 25, 0)
+        pin_b, ppad_b = tft.tft_footprint(2, R_PROD, 0, 1)
+        extra = {
+            "tft_n17838137": {
+                "forward_ms": statistics.median(fwd_ms),
+                "inverse_ms": statistics.median(inv_ms),
+                "forward_mcoeffs": TFT_N / statistics.median(fwd_ms) / 1e3,
+                "inverse_mcoeffs": TFT_N / statistics.median(inv_ms) / 1e3,
+                "roundtrip_identity": ok,
+                "device_bytes_inplace": inplace_b,
+                "device_bytes_padded_2^25": padded_b},
+            "polymul_footprint": {"device_bytes_inplace": pin_b,
+                                  "device_bytes_padded": ppad_b},
+        }
+        # ---- end to end through the host-buffer entry point --------------
+        out_pin = torch.empty(R_PROD, dtype=torch.int64).pin_memory()
+        for _ in range(2):
+            tft.tft_polymul_host(ctx, a_pin, b_pin, out_pin, stream)
+        e2e_s = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            tft.tft_polymul_host(ctx, a_pin, b_pin, out_pin, stream)
+            e2e_s.append(time.perf_counter() - t0)
+        same = bool(torch.equal(out_pin, out.cpu()))
+        e2e = {"value": R_PROD / statistics.mean(e2e_s) / 1e6,
+               "unit": "Mcoeff/s",
+               "h2d_bytes_per_step": (NA + NB) * 8,
+               "d2h_bytes_per_step": R_PROD * 8,
+               "ms_per_step": 1e3 * statistics.mean(e2e_s),
+               "matches_device_result": same}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, cores, desc, _ = oracle_polymul_sample(scale=0.125)
+        cpu = {"value": v, "unit": "Mcoeff/s", "cores": cores,
+               "kind": "oracle", "sample": desc}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mcoeff/s",
+        "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": total_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic: uniform residues mod p, seed 2",
+        "config": {"workload": WORKLOAD, "na": NA, "nb": NB, "r": R_PROD,
+                   "prime": "2^64-2^32+1",
+                   "l2": "flushed between timed steps (256 MiB write "
+                         "outside the per-step events)",
+                   "parallelism": f"replicas x{world}",
+                   "plan": plan},
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "roofline": roof,
+        "hbm_view": {"algorithmic_bytes_per_step": alg_bytes,
+                     "frac_of_hbm": hbm_frac, "hbm_peak_gbs": hbm_peak,
+                     "peak_source": hbm_src},
+        "kernels": kernels,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "wall_s_timed_loop": wall,
+        "extra": extra,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

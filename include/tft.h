@@ -1,0 +1,203 @@
+/*
+ * tft.h -- C ABI of the GB300 in-place truncated Fourier transform library.
+ *
+ * What it computes (Harvey & Roche, "An in-place truncated Fourier transform
+ * and applications to polynomial multiplication", 2010):
+ *
+ *   Ring (Section 2.1): Z/p for one of three primes p = c 2^K + 1; 2 is
+ *   invertible and primitive 2^k-th roots exist for every k <= K.
+ *
+ *   Roots (Section 2.2): compatible primitive roots omega_[k],
+ *   omega_[k+1]^2 = omega_[k].  The paper leaves the choice open; this
+ *   library fixes omega_[K] = g^((p-1)/2^K) with the generator g below and
+ *   omega_[k] = omega_[K]^(2^(K-k)).  Then omega_s = omega_[K]^(rev_K s).
+ *
+ *     prime                 storage  K   g    omega_[K]
+ *     998244353             uint32   23  3    15311432
+ *     2013265921            uint32   27  31   440564289
+ *     2^64 - 2^32 + 1       uint64   32  7    1753635133440165772
+ *
+ *   TFT (Section 2.2, Algorithm 1): for x_0..x_{n-1} (coefficients of F,
+ *   deg F < n) the transform overwrites x with F^_s = F(omega_s), s < n.
+ *   The output is in this bit-reversed-root order, not natural DFT order.
+ *   It equals the first n outputs of the length-2^k transform of x padded
+ *   with zeros for any n <= 2^k (Section 1.2); with compatible roots it does
+ *   not depend on k, which is therefore only validated.
+ *
+ *   ITFT (Section 4, Algorithm 2): the inverse map, in place.
+ *
+ *   Product (Sections 1.2 and 5): C = A B of length r = na + nb - 1 by a TFT
+ *   of both zero-extended operands, the pointwise product C^_s = A^_s B^_s,
+ *   and an ITFT.
+ *
+ * Elements are canonical residues in [0, p): uint32_t for the two 32-bit
+ * primes, uint64_t for 2^64 - 2^32 + 1.  Inputs outside [0, p) are not
+ * checked and give unspecified (but memory-safe) results.  All arithmetic is
+ * exact; results are bit-for-bit those of the definitions above.
+ *
+ * Memory: transforms run in place on the caller's n-word device buffer; the
+ * context owns a fixed scratch of at most 3 * 2^14 words plus, for products,
+ * one r-word work buffer, all reserved when the context is created.  No call
+ * allocates device memory.
+ *
+ * Errors: argument errors are returned synchronously and nothing is
+ * launched.  Launch failures return TFT_ECUDA.  Kernels run asynchronously
+ * on the given stream; faults that surface later are reported by
+ * tft_last_error() after the stream has been synchronized.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  Calls on one context must not overlap on the GPU: the
+ * context's scratch is shared by every call (use one context per concurrent
+ * stream).
+ */
+#ifndef TFT_GB300_H
+#define TFT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tft_prime {
+  TFT_P998244353 = 0,  /* 119 * 2^23 + 1, uint32 elements */
+  TFT_P2013265921 = 1, /*  15 * 2^27 + 1, uint32 elements */
+  TFT_PGOLDILOCKS = 2  /* 2^64 - 2^32 + 1, uint64 elements */
+} tft_prime;
+
+typedef enum tft_status {
+  TFT_OK = 0,
+  TFT_EINVAL = 1,   /* bad argument: null or misaligned pointer, n = 0,
+                       n > 2^k, k > K, aliasing output, unknown prime */
+  TFT_ERANGE = 2,   /* size beyond this context's max_len or the supported
+                       maximum (2^25 words for 2^64-2^32+1, 2^27 otherwise) */
+  TFT_ENOMEM = 3,   /* device allocation failed (context creation only) */
+  TFT_ECUDA = 4,    /* a CUDA runtime call or launch failed */
+  TFT_ETIMEOUT = 5  /* a bounded device-side wait expired */
+} tft_status;
+
+typedef struct tft_ctx tft_ctx;
+
+/* Context-creation flags. */
+#define TFT_CTX_HOST_STAGING 1u /* also reserve device staging buffers for
+                                   the *_host entry points (3 max_len words) */
+
+/*
+ * Create a context for `prime` on CUDA device `device`.  Transforms of length
+ * n <= max_len and products with r = na + nb - 1 <= max_len are accepted.
+ * Reserves the root table, the fixed scratch and (products) a max_len-word
+ * work buffer on the device.  On success *out owns them until
+ * tft_ctx_destroy.  Errors: TFT_EINVAL (bad prime/device/out, max_len = 0),
+ * TFT_ERANGE (max_len beyond the supported maximum), TFT_ENOMEM, TFT_ECUDA.
+ */
+tft_status tft_ctx_create(tft_prime prime, int device, uint64_t max_len,
+                          uint32_t flags, tft_ctx** out);
+
+/* Free a context (waits for nothing: synchronize its streams first). */
+tft_status tft_ctx_destroy(tft_ctx* ctx);
+
+/*
+ * tft(x, n, k): in-place forward TFT, Algorithm 1 (Section 3).
+ *   x      device pointer, n elements, 16-byte aligned; overwritten with
+ *          F^_s = F(omega_s), s < n.
+ *   n      1 <= n <= 2^k and n <= max_len.
+ *   k      log2 of the transform size the caller has in mind, n <= 2^k,
+ *          k <= K(prime).  The result does not depend on k.
+ */
+tft_status tft_forward(tft_ctx* ctx, void* x, uint64_t n, uint32_t k,
+                       void* stream);
+
+/*
+ * itft(X, n, k): in-place inverse TFT, Algorithm 2 (Section 4).  Same
+ * arguments as tft_forward; X holds F^_0..F^_{n-1} and is overwritten with
+ * F_0..F_{n-1}.
+ */
+tft_status tft_inverse(tft_ctx* ctx, void* X, uint64_t n, uint32_t k,
+                       void* stream);
+
+/*
+ * polymul(a, b): out = a * b mod p (Section 5; TFT of both operands,
+ * pointwise product, ITFT).
+ *   a, b   device pointers, na and nb elements (read only; may alias each
+ *          other), 16-byte aligned.
+ *   out    device pointer, r = na + nb - 1 elements, 16-byte aligned, must
+ *          not overlap a or b.
+ * Uses the context's r-word work buffer.  Errors as above.
+ */
+tft_status tft_polymul(tft_ctx* ctx, const void* a, uint64_t na,
+                       const void* b, uint64_t nb, void* out, void* stream);
+
+/*
+ * Host-buffer variants: the same operations on HOST buffers.  Each call
+ * copies the inputs to the context's staging buffers (cudaMemcpyAsync on
+ * `stream`), runs the transform or product there, copies the result back and
+ * synchronizes `stream` before returning.  Pinned host memory gives full
+ * copy bandwidth.  Requires a context created with TFT_CTX_HOST_STAGING.
+ */
+tft_status tft_forward_host(tft_ctx* ctx, void* x_host, uint64_t n,
+                            uint32_t k, void* stream);
+tft_status tft_inverse_host(tft_ctx* ctx, void* X_host, uint64_t n,
+                            uint32_t k, void* stream);
+tft_status tft_polymul_host(tft_ctx* ctx, const void* a_host, uint64_t na,
+                            const void* b_host, uint64_t nb, void* out_host,
+                            void* stream);
+
+/*
+ * Device memory footprint of one operation, next to a padded power-of-two
+ * NTT (van der Hoeven's TFT and the plain NTT both work in a 2^k buffer,
+ * Section 1.2).
+ *   op = 0 (transform, either direction): *inplace_bytes = n words + the
+ *          context scratch the plan uses; *padded_bytes = 2^k words.
+ *   op = 1 (product, n = r = na + nb - 1, k = ceil(lg r) if 0 is passed):
+ *          *inplace_bytes = out (r words) + work (r words) + scratch;
+ *          *padded_bytes = two 2^k-word buffers.
+ * Pure host computation; no device is touched.
+ */
+tft_status tft_footprint(tft_prime prime, uint64_t n, uint32_t k, int op,
+                         uint64_t* inplace_bytes, uint64_t* padded_bytes);
+
+/*
+ * Execution plan chosen for length n (host only), for diagnostics and
+ * benchmarks: out[0] = 1 if the single-CTA path is used, out[1] = its log2
+ * padded length; out[2] = lr (rows of 2^lr), out[3] = c (columns padded to
+ * 2^c), out[4] = log2 columns per CTA, out[5] = a, out[6] = b,
+ * out[7] = row CTAs per SM.  Returns TFT_ERANGE when n is unsupported.
+ */
+tft_status tft_describe_plan(tft_prime prime, uint64_t n, int64_t out[8]);
+
+/* Bytes per element: 4 or 8. 0 for an unknown prime. */
+uint32_t tft_element_bytes(tft_prime prime);
+
+/* Sticky device-side status of a context (TFT_OK, TFT_ECUDA, TFT_ETIMEOUT).
+ * Call after synchronizing the context's streams. */
+tft_status tft_last_error(tft_ctx* ctx);
+
+/* Static description of a status code. */
+const char* tft_status_string(tft_status s);
+
+/* Name of the CUDA error behind the calling thread's last TFT_ECUDA
+ * ("no error" if none); a static string. */
+const char* tft_last_cuda_error(void);
+
+/*
+ * Launch accounting and per-kernel timing.  Every kernel the library
+ * launches is counted per context (tft_launch_count).  With profiling
+ * enabled the library also records a CUDA event pair on the call's stream
+ * around each launch; tft_profile_read (after the streams are synchronized)
+ * returns, per kernel kind 0 .. TFT_NUM_KERNEL_KINDS-1, the summed duration
+ * in milliseconds and the number of timed launches since the last
+ * tft_profile_enable (which resets the totals).  Kind names come from
+ * tft_kernel_name.  Profiling must be off while a stream is being captured
+ * into a CUDA graph.
+ */
+#define TFT_NUM_KERNEL_KINDS 8
+tft_status tft_profile_enable(tft_ctx* ctx, int enable);
+tft_status tft_profile_read(tft_ctx* ctx, double* ms, uint64_t* launches);
+const char* tft_kernel_name(int kind);
+uint64_t tft_launch_count(tft_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFT_GB300_H */

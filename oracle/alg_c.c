@@ -15,6 +15,7 @@
  *   orc_eval         F(z) by Horner
  *   orc_eval_tft_points   F(omega_s) for chosen s (the definition, Sec. 2.2)
  *   orc_schoolbook   c_t = sum_i a_i b_{t-i}
+ *   orc_conv_coeff   one coefficient c_t of the product, by that sum
  *   orc_fft_pow2     textbook radix-2 DIF FFT, natural in, bit-reversed out
  *
  * Prime ids: 0 -> 998244353 (g = 3), 1 -> 2013265921 (g = 31),
@@ -305,4 +306,17 @@ int orc_fft_pow2(int id, uint64_t *X, uint64_t N) {
         }
     }
     return 0;
+}
+
+/* c_t = sum_{i} a_i b_{t-i} over 0 <= i < na, 0 <= t-i < nb. */
+uint64_t orc_conv_coeff(int id, const uint64_t *a, uint64_t na,
+                        const uint64_t *b, uint64_t nb, uint64_t t) {
+    if (!valid_id(id)) return 0;
+    const uint64_t p = PRIMES[id].p;
+    uint64_t lo = t + 1 > nb ? t + 1 - nb : 0;
+    uint64_t hi = t < na - 1 ? t : na - 1;
+    uint64_t acc = 0;
+    for (uint64_t i = lo; i <= hi && i < na; i++)
+        acc = addm(acc, mulm(a[i], b[t - i], p), p);
+    return acc;
 }

@@ -59,6 +59,9 @@ def lib():
         L.orc_eval.restype = ctypes.c_uint64
         L.orc_eval.argtypes = [ctypes.c_int, _u64p, ctypes.c_uint64,
                                ctypes.c_uint64]
+        L.orc_conv_coeff.restype = ctypes.c_uint64
+        L.orc_conv_coeff.argtypes = [ctypes.c_int, _u64p, ctypes.c_uint64,
+                                     _u64p, ctypes.c_uint64, ctypes.c_uint64]
         L.orc_eval_tft_points.restype = ctypes.c_int
         L.orc_eval_tft_points.argtypes = [ctypes.c_int, _u64p, ctypes.c_uint64,
                                           _u64p, ctypes.c_uint64, _u64p]
@@ -142,6 +145,14 @@ def eval_tft_points(prime, x, points):
     if rc:
         raise ValueError("orc_eval_tft_points failed")
     return out
+
+
+def conv_coeff(prime, a, b, t):
+    """One coefficient c_t = sum_i a_i b_{t-i} of the product (definition)."""
+    A = _as_u64(a)
+    B = _as_u64(b)
+    return int(lib().orc_conv_coeff(_pid(prime), _ptr(A), A.size, _ptr(B),
+                                    B.size, int(t)))
 
 
 def omega(prime, s):

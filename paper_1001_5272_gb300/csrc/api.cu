@@ -1,0 +1,612 @@
+// C ABI (include/tft.h): argument checking, planning, context management.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "../../include/tft.h"
+#include "field.cuh"
+#include "tft_internal.h"
+
+using namespace tftgb;
+
+namespace {
+
+typedef unsigned __int128 u128;
+
+struct PrimeInfo {
+  uint64_t p;
+  int K;
+  uint64_t g;
+  uint32_t w;  // element bytes
+};
+
+const PrimeInfo kPrimes[3] = {
+    {998244353ull, 23, 3, 4},
+    {2013265921ull, 27, 31, 4},
+    {0xFFFFFFFF00000001ull, 32, 7, 8},
+};
+
+uint64_t mulm(uint64_t a, uint64_t b, uint64_t p) {
+  return (uint64_t)(((u128)a * b) % p);
+}
+uint64_t powm(uint64_t a, uint64_t e, uint64_t p) {
+  uint64_t r = 1 % p;
+  a %= p;
+  while (e) {
+    if (e & 1) r = mulm(r, a, p);
+    a = mulm(a, a, p);
+    e >>= 1;
+  }
+  return r;
+}
+uint64_t rev_bits(uint64_t s, int k) {
+  uint64_t o = 0;
+  for (int i = 0; i < k; i++) {
+    o = (o << 1) | (s & 1);
+    s >>= 1;
+  }
+  return o;
+}
+// omega_s = omega_[K]^(rev_K s)
+uint64_t omega_s(const PrimeInfo& pr, uint64_t s) {
+  uint64_t top = powm(pr.g, (pr.p - 1) >> pr.K, pr.p);
+  return powm(top, rev_bits(s, pr.K), pr.p);
+}
+// twiddle form: Montgomery (x 2^32) for the 32-bit primes, identity otherwise
+uint64_t to_tw(const PrimeInfo& pr, uint64_t x) {
+  if (pr.w == 8) return x % pr.p;
+  return (uint64_t)((((u128)(x % pr.p)) << 32) % pr.p);
+}
+
+int ceil_log2(uint64_t n) {
+  int l = 0;
+  while ((1ull << l) < n) ++l;
+  return l;
+}
+
+bool valid_prime(int prime) { return prime >= 0 && prime < 3; }
+
+// Largest transform length the two-pass plan handles.
+uint64_t max_supported(const PrimeInfo& pr) {
+  return pr.w == 8 ? (1ull << 25) : (1ull << 27);
+}
+
+// Choose the plan for length n (see tft_internal.h).  Returns false if n is
+// beyond the supported range.
+bool make_plan(int prime, uint64_t n, Plan* out) {
+  const PrimeInfo& pr = kPrimes[prime];
+  Plan P;
+  memset(&P, 0, sizeof(P));
+  const int small_l = pr.w == 8 ? 12 : 13;
+  const int lr_max = pr.w == 8 ? 13 : 14;
+  const int c_max = pr.w == 8 ? 12 : 13;
+  if (n == 0 || n > max_supported(pr)) return false;
+  if (n <= (1ull << small_l)) {
+    P.small = 1;
+    P.l = ceil_log2(n);
+    P.row_ctas_per_sm = 1;
+    *out = P;
+    return true;
+  }
+  const int lg = ceil_log2(n);
+  int lr = (lg + 1) / 2;
+  if (lr < 6) lr = 6;
+  if (lr > lr_max) lr = lr_max;
+  // column rows: a, plus one row for the long columns' last entries and the
+  // short columns' E_q when b > 0
+  auto col_rows = [&](int lrr) {
+    return (n >> lrr) + ((n & ((1ull << lrr) - 1)) ? 1 : 0);
+  };
+  while (col_rows(lr) > (1ull << c_max)) {
+    if (++lr > lr_max) return false;
+  }
+  P.lr = lr;
+  P.a = n >> lr;
+  P.b = n & ((1ull << lr) - 1);
+  P.c = ceil_log2(col_rows(lr));
+  // columns per CTA: the most (<= 16, <= R) whose tile fits ~200 KB
+  const size_t budget = 200 * 1024;
+  int clog = 0;
+  while (clog < 4 && (1 << (clog + 1)) <= (1 << lr)) {
+    Plan Q = P;
+    Q.clog = clog + 1;
+    if (plan_smem(prime, Q).col > budget) break;
+    ++clog;
+  }
+  P.clog = clog;
+  const size_t srow = plan_smem(prime, P).row;
+  int per_sm = (int)((228 * 1024) / (srow + 1024));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 4) per_sm = 4;
+  P.row_ctas_per_sm = per_sm;
+  *out = P;
+  return true;
+}
+
+// RAII switch to the context's device.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
+      cudaSetDevice(prev);
+  }
+};
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+bool overlap(const void* a, uint64_t abytes, const void* b, uint64_t bbytes) {
+  const uintptr_t a0 = (uintptr_t)a, a1 = a0 + abytes;
+  const uintptr_t b0 = (uintptr_t)b, b1 = b0 + bbytes;
+  return a0 < b1 && b0 < a1;
+}
+
+}  // namespace
+
+constexpr int kProfSlots = 64;
+
+struct ProfSlot {
+  cudaEvent_t start;
+  cudaEvent_t stop;
+  int kind;
+};
+
+struct tft_ctx {
+  int prime;
+  int device;
+  int nsm;
+  uint64_t max_len;
+  uint32_t flags;
+  PrimeInfo pr;
+  alignas(16) unsigned char rt[sizeof(RootTable<uint64_t>)];
+  void* scratch;     // 3 * 2^14 words: E / EA, EB
+  void* work;        // max_len words (products)
+  void* stage;       // 3 * max_len words (host-buffer entry points)
+  tft_status sticky;
+  // launch accounting and optional per-kernel timing
+  uint64_t launches;
+  int prof_on;
+  int prof_pending;
+  ProfSlot prof[kProfSlots];
+  double prof_ms[K_NUM_KINDS];
+  uint64_t prof_count[K_NUM_KINDS];
+  LaunchHook hook;
+};
+
+namespace {
+
+void build_root_table(tft_ctx* c) {
+  const PrimeInfo& pr = c->pr;
+  const uint64_t top = powm(pr.g, (pr.p - 1) >> pr.K, pr.p);
+  uint64_t w[33], wi[33];
+  for (int j = 0; j <= 32; ++j) {
+    if (j > pr.K) {
+      w[j] = wi[j] = 0;
+      continue;
+    }
+    uint64_t v = top;
+    for (int i = 0; i < pr.K - j; ++i) v = mulm(v, v, pr.p);
+    w[j] = v;
+    wi[j] = powm(v, pr.p - 2, pr.p);
+  }
+  const uint64_t half = (pr.p + 1) / 2;
+  if (pr.w == 8) {
+    RootTable<uint64_t> t;
+    for (int j = 0; j <= 32; ++j) {
+      t.w[j] = to_tw(pr, w[j]);
+      t.winv[j] = to_tw(pr, wi[j]);
+    }
+    t.half_tw = to_tw(pr, half);
+    t.one_tw = to_tw(pr, 1);
+    memcpy(c->rt, &t, sizeof(t));
+  } else {
+    RootTable<uint32_t> t;
+    for (int j = 0; j <= 32; ++j) {
+      t.w[j] = (uint32_t)to_tw(pr, w[j]);
+      t.winv[j] = (uint32_t)to_tw(pr, wi[j]);
+    }
+    t.half_tw = (uint32_t)to_tw(pr, half);
+    t.one_tw = (uint32_t)to_tw(pr, 1);
+    memcpy(c->rt, &t, sizeof(t));
+  }
+}
+
+// The Montgomery constants compiled into field.cuh must match the moduli.
+bool check_constants() {
+  auto chk = [](uint32_t p, uint32_t pinv, uint32_t r2, uint32_t one) {
+    return (uint32_t)(p * pinv) == 0xFFFFFFFFu &&
+           r2 == (uint32_t)(((u128)1 << 64) % p) &&
+           one == (uint32_t)(((uint64_t)1 << 32) % p);
+  };
+  return chk(P998::P, P998::PINV, P998::R2, P998::ONE) &&
+         chk(P2013::P, P2013::PINV, P2013::R2, P2013::ONE);
+}
+
+std::mutex g_prep_mu;
+bool g_prepared[3][64] = {};
+
+thread_local const char* g_last_cuda_error = "no error";
+
+cudaError_t note(cudaError_t e) {
+  if (e != cudaSuccess) g_last_cuda_error = cudaGetErrorName(e);
+  return e;
+}
+
+void prof_drain(tft_ctx* c) {
+  for (int i = 0; i < c->prof_pending; ++i) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(c->prof[i].stop) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, c->prof[i].start, c->prof[i].stop) ==
+            cudaSuccess) {
+      c->prof_ms[c->prof[i].kind] += ms;
+      c->prof_count[c->prof[i].kind] += 1;
+    }
+  }
+  c->prof_pending = 0;
+}
+
+void hook_before(void* user, int kind, cudaStream_t s) {
+  tft_ctx* c = (tft_ctx*)user;
+  if (!c->prof_on) return;
+  if (c->prof_pending == kProfSlots) prof_drain(c);
+  cudaEventRecord(c->prof[c->prof_pending].start, s);
+  (void)kind;
+}
+
+void hook_after(void* user, int kind, cudaStream_t s) {
+  tft_ctx* c = (tft_ctx*)user;
+  c->launches++;
+  if (!c->prof_on) return;
+  ProfSlot& sl = c->prof[c->prof_pending];
+  cudaEventRecord(sl.stop, s);
+  sl.kind = kind;
+  c->prof_pending++;
+}
+
+tft_status check_transform_args(tft_ctx* ctx, const void* x, uint64_t n,
+                                uint32_t k) {
+  if (!ctx || !x) return TFT_EINVAL;
+  if (n == 0) return TFT_EINVAL;
+  if ((int)k > ctx->pr.K) return TFT_EINVAL;
+  if (k < 64 && n > (1ull << k)) return TFT_EINVAL;
+  if (!aligned16(x)) return TFT_EINVAL;
+  if (n > ctx->max_len) return TFT_ERANGE;
+  return TFT_OK;
+}
+
+tft_status from_cuda(tft_ctx* ctx, cudaError_t e) {
+  if (e == cudaSuccess) return TFT_OK;
+  note(e);
+  if (ctx) ctx->sticky = TFT_ECUDA;
+  return TFT_ECUDA;
+}
+
+uint64_t omega_a_tw(tft_ctx* ctx, const Plan& P) {
+  return to_tw(ctx->pr, omega_s(ctx->pr, P.a));
+}
+
+}  // namespace
+
+extern "C" {
+
+tft_status tft_ctx_create(tft_prime prime, int device, uint64_t max_len,
+                          uint32_t flags, tft_ctx** out) {
+  if (!out) return TFT_EINVAL;
+  *out = nullptr;
+  if (!valid_prime((int)prime) || max_len == 0 || device < 0)
+    return TFT_EINVAL;
+  if (!check_constants()) return TFT_EINVAL;
+  const PrimeInfo& pr = kPrimes[(int)prime];
+  if (max_len > max_supported(pr)) return TFT_ERANGE;
+  int ndev = 0;
+  if (note(cudaGetDeviceCount(&ndev)) != cudaSuccess) return TFT_ECUDA;
+  if (device >= ndev) return TFT_EINVAL;
+  DeviceGuard g(device);
+  if (!g.ok) return TFT_ECUDA;
+  {
+    std::lock_guard<std::mutex> lk(g_prep_mu);
+    if (device < 64 && !g_prepared[(int)prime][device]) {
+      int optin = 0;
+      if (note(cudaDeviceGetAttribute(&optin,
+                                      cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                      device)) != cudaSuccess)
+        return TFT_ECUDA;
+      if (note(prepare_kernels((int)prime, (size_t)optin)) != cudaSuccess)
+        return TFT_ECUDA;
+      g_prepared[(int)prime][device] = true;
+    }
+  }
+  tft_ctx* c = (tft_ctx*)calloc(1, sizeof(tft_ctx));
+  if (!c) return TFT_ENOMEM;
+  c->prime = (int)prime;
+  c->device = device;
+  c->max_len = max_len;
+  c->flags = flags;
+  c->pr = pr;
+  c->sticky = TFT_OK;
+  if (cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount,
+                             device) != cudaSuccess) {
+    free(c);
+    return TFT_ECUDA;
+  }
+  build_root_table(c);
+  c->hook.before = hook_before;
+  c->hook.after = hook_after;
+  c->hook.user = c;
+  for (int i = 0; i < kProfSlots; ++i) {
+    if (note(cudaEventCreate(&c->prof[i].start)) != cudaSuccess ||
+        note(cudaEventCreate(&c->prof[i].stop)) != cudaSuccess) {
+      for (int j = 0; j <= i; ++j) {
+        if (c->prof[j].start) cudaEventDestroy(c->prof[j].start);
+        if (c->prof[j].stop) cudaEventDestroy(c->prof[j].stop);
+      }
+      free(c);
+      return TFT_ECUDA;
+    }
+  }
+  const size_t w = pr.w;
+  if (cudaMalloc(&c->scratch, 3 * (1ull << 14) * w) != cudaSuccess) {
+    for (int i = 0; i < kProfSlots; ++i) {
+      cudaEventDestroy(c->prof[i].start);
+      cudaEventDestroy(c->prof[i].stop);
+    }
+    free(c);
+    return TFT_ENOMEM;
+  }
+  if (cudaMalloc(&c->work, max_len * w) != cudaSuccess) {
+    cudaFree(c->scratch);
+    free(c);
+    return TFT_ENOMEM;
+  }
+  if (flags & TFT_CTX_HOST_STAGING) {
+    if (cudaMalloc(&c->stage, 3 * max_len * w) != cudaSuccess) {
+      cudaFree(c->work);
+      cudaFree(c->scratch);
+      free(c);
+      return TFT_ENOMEM;
+    }
+  }
+  *out = c;
+  return TFT_OK;
+}
+
+tft_status tft_ctx_destroy(tft_ctx* ctx) {
+  if (!ctx) return TFT_EINVAL;
+  DeviceGuard g(ctx->device);
+  for (int i = 0; i < kProfSlots; ++i) {
+    if (ctx->prof[i].start) cudaEventDestroy(ctx->prof[i].start);
+    if (ctx->prof[i].stop) cudaEventDestroy(ctx->prof[i].stop);
+  }
+  if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->work) cudaFree(ctx->work);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  free(ctx);
+  return TFT_OK;
+}
+
+tft_status tft_forward(tft_ctx* ctx, void* x, uint64_t n, uint32_t k,
+                       void* stream) {
+  tft_status st = check_transform_args(ctx, x, n, k);
+  if (st != TFT_OK) return st;
+  Plan P;
+  if (!make_plan(ctx->prime, n, &P)) return TFT_ERANGE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  return from_cuda(ctx, launch_forward(ctx->prime, x, n, P, ctx->scratch,
+                                       ctx->rt, ctx->nsm,
+                                       (cudaStream_t)stream, &ctx->hook));
+}
+
+tft_status tft_inverse(tft_ctx* ctx, void* X, uint64_t n, uint32_t k,
+                       void* stream) {
+  tft_status st = check_transform_args(ctx, X, n, k);
+  if (st != TFT_OK) return st;
+  Plan P;
+  if (!make_plan(ctx->prime, n, &P)) return TFT_ERANGE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  return from_cuda(ctx, launch_inverse(ctx->prime, X, n, P, ctx->scratch,
+                                       P.small ? 0 : omega_a_tw(ctx, P),
+                                       ctx->rt, ctx->nsm,
+                                       (cudaStream_t)stream, &ctx->hook));
+}
+
+tft_status tft_polymul(tft_ctx* ctx, const void* a, uint64_t na,
+                       const void* b, uint64_t nb, void* out, void* stream) {
+  if (!ctx || !a || !b || !out || na == 0 || nb == 0) return TFT_EINVAL;
+  if (!aligned16(a) || !aligned16(b) || !aligned16(out)) return TFT_EINVAL;
+  const uint64_t r = na + nb - 1;
+  const size_t w = ctx->pr.w;
+  if (overlap(out, r * w, a, na * w) || overlap(out, r * w, b, nb * w))
+    return TFT_EINVAL;
+  if (r > ctx->max_len) return TFT_ERANGE;
+  Plan P;
+  if (!make_plan(ctx->prime, r, &P)) return TFT_ERANGE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  unsigned char* s = (unsigned char*)ctx->scratch;
+  void* EA = s;
+  void* EB = s + (1ull << 14) * w;
+  return from_cuda(ctx, launch_polymul(ctx->prime, a, na, b, nb, out, P,
+                                       ctx->work, EA, EB,
+                                       P.small ? 0 : omega_a_tw(ctx, P),
+                                       ctx->rt, ctx->nsm,
+                                       (cudaStream_t)stream, &ctx->hook));
+}
+
+static tft_status host_transform(tft_ctx* ctx, void* xh, uint64_t n,
+                                 uint32_t k, void* stream, bool inv) {
+  if (!ctx || !xh) return TFT_EINVAL;
+  if (!(ctx->flags & TFT_CTX_HOST_STAGING) || !ctx->stage) return TFT_EINVAL;
+  if (n == 0) return TFT_EINVAL;
+  if (n > ctx->max_len) return TFT_ERANGE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = n * ctx->pr.w;
+  if (cudaMemcpyAsync(ctx->stage, xh, bytes, cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return from_cuda(ctx, cudaErrorUnknown);
+  tft_status st = inv ? tft_inverse(ctx, ctx->stage, n, k, stream)
+                      : tft_forward(ctx, ctx->stage, n, k, stream);
+  if (st != TFT_OK) {
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  if (cudaMemcpyAsync(xh, ctx->stage, bytes, cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return from_cuda(ctx, cudaErrorUnknown);
+  return from_cuda(ctx, cudaStreamSynchronize(s));
+}
+
+tft_status tft_forward_host(tft_ctx* ctx, void* x_host, uint64_t n,
+                            uint32_t k, void* stream) {
+  return host_transform(ctx, x_host, n, k, stream, false);
+}
+
+tft_status tft_inverse_host(tft_ctx* ctx, void* X_host, uint64_t n,
+                            uint32_t k, void* stream) {
+  return host_transform(ctx, X_host, n, k, stream, true);
+}
+
+tft_status tft_polymul_host(tft_ctx* ctx, const void* a_host, uint64_t na,
+                            const void* b_host, uint64_t nb, void* out_host,
+                            void* stream) {
+  if (!ctx || !a_host || !b_host || !out_host || na == 0 || nb == 0)
+    return TFT_EINVAL;
+  if (!(ctx->flags & TFT_CTX_HOST_STAGING) || !ctx->stage) return TFT_EINVAL;
+  const uint64_t r = na + nb - 1;
+  if (r > ctx->max_len) return TFT_ERANGE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  const size_t w = ctx->pr.w;
+  // staging layout: [out: max_len][a: max_len][b: max_len], each 16-B aligned
+  unsigned char* base = (unsigned char*)ctx->stage;
+  void* dout = base;
+  void* da = base + ctx->max_len * w;
+  void* db = base + 2 * ctx->max_len * w;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(da, a_host, na * w, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(db, b_host, nb * w, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+    return from_cuda(ctx, cudaErrorUnknown);
+  tft_status st = tft_polymul(ctx, da, na, db, nb, dout, stream);
+  if (st != TFT_OK) {
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  if (cudaMemcpyAsync(out_host, dout, r * w, cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return from_cuda(ctx, cudaErrorUnknown);
+  return from_cuda(ctx, cudaStreamSynchronize(s));
+}
+
+tft_status tft_footprint(tft_prime prime, uint64_t n, uint32_t k, int op,
+                         uint64_t* inplace_bytes, uint64_t* padded_bytes) {
+  if (!valid_prime((int)prime) || !inplace_bytes || !padded_bytes || n == 0)
+    return TFT_EINVAL;
+  const PrimeInfo& pr = kPrimes[(int)prime];
+  if (k == 0) k = (uint32_t)ceil_log2(n);
+  if ((int)k > pr.K || (k < 64 && n > (1ull << k))) return TFT_EINVAL;
+  Plan P;
+  if (!make_plan((int)prime, n, &P)) return TFT_ERANGE;
+  const uint64_t w = pr.w;
+  const uint64_t R = P.small ? 0 : (1ull << P.lr);
+  if (op == 0) {
+    *inplace_bytes = (n + (P.b ? R : 0)) * w;
+    *padded_bytes = (1ull << k) * w;
+  } else if (op == 1) {
+    *inplace_bytes = (2 * n + (P.small ? 0 : 2 * R)) * w;
+    *padded_bytes = 2 * (1ull << k) * w;
+  } else {
+    return TFT_EINVAL;
+  }
+  return TFT_OK;
+}
+
+tft_status tft_describe_plan(tft_prime prime, uint64_t n, int64_t out[8]) {
+  if (!valid_prime((int)prime) || !out) return TFT_EINVAL;
+  Plan P;
+  if (!make_plan((int)prime, n, &P)) return TFT_ERANGE;
+  out[0] = P.small;
+  out[1] = P.l;
+  out[2] = P.lr;
+  out[3] = P.c;
+  out[4] = P.clog;
+  out[5] = (int64_t)P.a;
+  out[6] = (int64_t)P.b;
+  out[7] = P.row_ctas_per_sm;
+  return TFT_OK;
+}
+
+uint32_t tft_element_bytes(tft_prime prime) {
+  return valid_prime((int)prime) ? kPrimes[(int)prime].w : 0;
+}
+
+tft_status tft_last_error(tft_ctx* ctx) {
+  if (!ctx) return TFT_EINVAL;
+  if (ctx->sticky != TFT_OK) return ctx->sticky;
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaPeekAtLastError();
+  return e == cudaSuccess ? TFT_OK : TFT_ECUDA;
+}
+
+tft_status tft_profile_enable(tft_ctx* ctx, int enable) {
+  if (!ctx) return TFT_EINVAL;
+  DeviceGuard g(ctx->device);
+  prof_drain(ctx);
+  for (int k = 0; k < K_NUM_KINDS; ++k) {
+    ctx->prof_ms[k] = 0.0;
+    ctx->prof_count[k] = 0;
+  }
+  ctx->prof_on = enable ? 1 : 0;
+  return TFT_OK;
+}
+
+tft_status tft_profile_read(tft_ctx* ctx, double* ms, uint64_t* launches) {
+  if (!ctx || !ms || !launches) return TFT_EINVAL;
+  DeviceGuard g(ctx->device);
+  prof_drain(ctx);
+  for (int k = 0; k < K_NUM_KINDS; ++k) {
+    ms[k] = ctx->prof_ms[k];
+    launches[k] = ctx->prof_count[k];
+  }
+  return TFT_OK;
+}
+
+const char* tft_kernel_name(int kind) {
+  static const char* names[K_NUM_KINDS] = {
+      "k_small", "k_small_mul", "k_col_fwd", "k_row_fwd",
+      "k_row_inv", "k_col_inv", "k_lastrow_inv", "k_row_mul"};
+  return (kind >= 0 && kind < K_NUM_KINDS) ? names[kind] : "unknown";
+}
+
+uint64_t tft_launch_count(tft_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+const char* tft_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char* tft_status_string(tft_status s) {
+  switch (s) {
+    case TFT_OK: return "ok";
+    case TFT_EINVAL: return "invalid argument";
+    case TFT_ERANGE: return "size out of range";
+    case TFT_ENOMEM: return "out of device memory";
+    case TFT_ECUDA: return "CUDA error";
+    case TFT_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Field arithmetic for the three NTT primes (device side).
+//
+// The paper works over any ring R in which 2 is not a zero-divisor and that
+// has the 2^k-th roots of unity it needs (Section 2.1).  The library
+// instantiates R = Z/p for
+//   p = 998244353        = 119 * 2^23 + 1   (uint32 storage, Montgomery form)
+//   p = 2013265921       =  15 * 2^27 + 1   (uint32 storage, Montgomery form)
+//   p = 2^64 - 2^32 + 1                      (uint64 storage, direct reduction)
+//
+// Data elements are always canonical residues in [0, p).  Twiddles are kept
+// in a per-field "twiddle form" that makes mul_tw(x, w) return x * w mod p in
+// canonical form:
+//   * 32-bit primes: w~ = w * 2^32 mod p and mul_tw is one Montgomery REDC of
+//     the 64-bit product (x * w~ * 2^-32 = x * w);
+//   * 2^64 - 2^32 + 1: w~ = w and mul_tw reduces the 128-bit product using
+//     2^64 = 2^32 - 1 and 2^96 = -1 (mod p).
+#pragma once
+#include <stdint.h>
+
+#ifndef TFT_HD
+#define TFT_HD __host__ __device__ __forceinline__
+#endif
+
+namespace tftgb {
+
+// ---------------------------------------------------------------------------
+// p = 2^64 - 2^32 + 1
+// ---------------------------------------------------------------------------
+struct Goldilocks {
+  using T = uint64_t;
+  static constexpr uint64_t P = 0xFFFFFFFF00000001ull;
+  static constexpr uint64_t EPS = 0xFFFFFFFFull;  // 2^64 mod p
+  static constexpr uint64_t HALF = 0x7FFFFFFF80000001ull;  // (p + 1) / 2
+  static constexpr int K = 32;                     // two-adicity
+  static constexpr int ID = 2;
+
+  static TFT_HD T add(T a, T b) {
+    T s = a + b;
+    // a carry out of 64 bits means the true sum is s + 2^64 = s + EPS (mod p)
+    // and then s + EPS < p; otherwise subtract p once if needed.
+    if (s < a) return s + EPS;
+    return s >= P ? s - P : s;
+  }
+  static TFT_HD T sub(T a, T b) {
+    T d = a - b;
+    return a < b ? d + P : d;  // wraps back into [0, p)
+  }
+  // x = lo + 2^64 (hl + 2^32 hh)  ==  lo + (2^32 - 1) hl - hh  (mod p)
+  static TFT_HD T reduce128(uint64_t lo, uint64_t hi) {
+    const uint32_t hl = (uint32_t)hi;
+    const uint32_t hh = (uint32_t)(hi >> 32);
+    uint64_t t0 = lo - hh;
+    if (lo < hh) t0 -= EPS;                      // borrow: wrapped by +2^64
+    const uint64_t t1 = ((uint64_t)hl << 32) - hl;  // hl * (2^32 - 1)
+    uint64_t r = t0 + t1;
+    if (r < t1) r += EPS;                        // carry: wrapped by -2^64
+    return r >= P ? r - P : r;
+  }
+  static __device__ __forceinline__ T mul(T a, T b) {
+    return reduce128(a * b, __umul64hi(a, b));
+  }
+  static __device__ __forceinline__ T mul_tw(T a, T w) { return mul(a, w); }
+  static __device__ __forceinline__ T mul_data(T a, T b) { return mul(a, b); }
+  static TFT_HD T half(T a) { return (a >> 1) + ((a & 1) ? HALF : 0); }
+  static TFT_HD T one_tw() { return 1; }
+};
+
+// ---------------------------------------------------------------------------
+// 32-bit primes in Montgomery form with R = 2^32.
+//   PINV = -p^{-1} mod 2^32, R2 = 2^64 mod p, ONE = 2^32 mod p.
+// ---------------------------------------------------------------------------
+template <uint32_t P_, uint32_t PINV_, uint32_t R2_, uint32_t ONE_, int K_,
+          int ID_>
+struct Mont32 {
+  using T = uint32_t;
+  static constexpr uint32_t P = P_;
+  static constexpr uint32_t PINV = PINV_;
+  static constexpr uint32_t R2 = R2_;
+  static constexpr uint32_t ONE = ONE_;
+  static constexpr int K = K_;
+  static constexpr int ID = ID_;
+
+  static TFT_HD T add(T a, T b) {
+    T s = a + b;  // < 2p < 2^32
+    return s >= P ? s - P : s;
+  }
+  static TFT_HD T sub(T a, T b) { return a >= b ? a - b : a - b + P; }
+  // t < p * 2^32  ->  t * 2^-32 mod p, canonical
+  static TFT_HD T redc(uint64_t t) {
+    const uint32_t m = (uint32_t)t * PINV;
+    const uint64_t u = (t + (uint64_t)m * P) >> 32;  // < 2p, no overflow
+    return (T)(u >= P ? u - P : u);
+  }
+  static TFT_HD T mul_tw(T a, T w) { return redc((uint64_t)a * w); }
+  static TFT_HD T mul_data(T a, T b) {
+    return redc((uint64_t)redc((uint64_t)a * b) * R2);
+  }
+  static TFT_HD T half(T a) { return (a + ((a & 1) ? P : 0)) >> 1; }
+  static TFT_HD T one_tw() { return ONE; }
+};
+
+// -p^{-1} mod 2^32, 2^64 mod p and 2^32 mod p for the two 32-bit primes
+// (checked on the host at context creation).
+using P998 = Mont32<998244353u, 998244351u, 932051910u, 301989884u, 23, 0>;
+using P2013 = Mont32<2013265921u, 2013265919u, 1172168163u, 268435454u, 27, 1>;
+
+// Root table passed by value to every kernel: omega_[j] (Section 2.2) in
+// twiddle form, and omega_[j]^{-1} / 2 in twiddle form, for j <= K.
+template <class T>
+struct RootTable {
+  T w[33];       // omega_[j]
+  T winv[33];    // omega_[j]^{-1}
+  T half_tw;     // 1/2 in twiddle form
+  T one_tw;      // 1 in twiddle form
+};
+
+}  // namespace tftgb

@@ -1,0 +1,603 @@
+// CUDA kernels of the in-place TFT / ITFT / TFT product for sm_103a.
+//
+// Decomposition (the L1 x L2 row/column split the paper credits to the
+// cache-friendly TFT, Section 1.3).  Fix R = 2^lr and write n = a R + b,
+// 0 <= b < R.  Column q (q < R) is C_q(x) = sum_t X_{q + tR} x^t, of length
+// a + 1 if q < b ("long") and a otherwise ("short"), so that
+//     F(x) = sum_q x^q C_q(x^R),
+//     F(omega_{rho R + j}) = sum_q omega_{rho R + j}^q C_q(omega_rho)
+// because omega_s^R = omega_{s >> lr} and omega_{rho R} omega_j =
+// omega_{rho R + j} (disjoint bits, Section 5).  Hence
+//   1. column pass: TFT of every column (its own TFT of length a or a+1,
+//      written back in place at stride R); short columns also need
+//      E_q = C_q(omega_a), which has no slot in the buffer and goes to an
+//      R-word scratch;
+//   2. row pass: every full row rho < a runs the last lr levels of the
+//      network (block rho of the global network) in place;
+//   3. last row rho = a: the first b outputs of block a, whose inputs are
+//      the long columns' last entries and E_q.
+// The inverse runs the same steps backwards: inverse rows; inverse short
+// columns (ITFT of length a) and E_q by Horner; the last row by the
+// generalized block inverse with known inputs E_q at q >= b; inverse long
+// columns (length a + 1).  Global memory holds the n-word buffer plus the
+// R-word scratch; every transform works in shared memory.
+#include <cuda_runtime.h>
+
+#include "engine.cuh"
+#include "tft_internal.h"
+
+namespace tftgb {
+
+template <class F>
+__device__ __forceinline__ void load_roots(RootTable<typename F::T>* s_rt,
+                                           const RootTable<typename F::T>& rt) {
+  using T = typename F::T;
+  const T* src = reinterpret_cast<const T*>(&rt);
+  T* dst = reinterpret_cast<T*>(s_rt);
+  constexpr int nwords = sizeof(RootTable<T>) / sizeof(T);
+  for (int i = threadIdx.x; i < nwords; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+template <class F>
+__device__ __forceinline__ typename F::T pow_tw(typename F::T base,
+                                                uint64_t e,
+                                                typename F::T one) {
+  typename F::T r = one;
+  while (e) {
+    if (e & 1) r = F::mul_tw(r, base);
+    base = F::mul_tw(base, base);
+    e >>= 1;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Small transforms: the whole transform of length n <= 2^l in one CTA.
+// ---------------------------------------------------------------------------
+template <class F, bool INV>
+__global__ void __launch_bounds__(512)
+k_small(typename F::T* __restrict__ x, uint32_t n, int l,
+        RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  load_roots<F>(&s_rt, rt);
+  T* Z = reinterpret_cast<T*>(smem_raw);
+  const uint32_t N = 1u << l;
+  T* W = Z + N;
+  T* Wih = W + (N > 1 ? N / 2 : 1);
+  build_base_tables<F>(W, INV ? Wih : nullptr, l, s_rt);
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
+    Z[i] = i < n ? x[i] : T(0);
+  __syncthreads();
+  ColTw<F> tw{W, Wih};
+  if (!INV)
+    fwd_pruned<F>(Z, 0, 0, l, n, tw);
+  else
+    inv_block<F>(Z, 0, 0, l, n, tw);
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = Z[i];
+}
+
+// Small TFT product: r = na + nb - 1 <= 2^l, both operands in one CTA.
+// The two operands are interleaved as the two columns of one tile.
+template <class F>
+__global__ void __launch_bounds__(512)
+k_small_mul(const typename F::T* __restrict__ a, uint32_t na,
+            const typename F::T* __restrict__ b, uint32_t nb,
+            typename F::T* __restrict__ out, int l,
+            RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  load_roots<F>(&s_rt, rt);
+  const uint32_t N = 1u << l;
+  const uint32_t r = na + nb - 1;
+  T* Z = reinterpret_cast<T*>(smem_raw);  // 2 N: (t, 0) = A, (t, 1) = B
+  T* W = Z + 2 * N;
+  T* Wih = W + (N > 1 ? N / 2 : 1);
+  build_base_tables<F>(W, Wih, l, s_rt);
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+    Z[2 * i] = i < na ? a[i] : T(0);
+    Z[2 * i + 1] = i < nb ? b[i] : T(0);
+  }
+  __syncthreads();
+  ColTw<F> tw{W, Wih};
+  fwd_pruned<F>(Z, 1, 1, l, r, tw);
+  for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
+    Z[2 * i] = i < r ? F::mul_data(Z[2 * i], Z[2 * i + 1]) : T(0);
+  __syncthreads();
+  inv_block<F>(Z, 0, 1, l, r, tw);
+  for (uint32_t i = threadIdx.x; i < r; i += blockDim.x) out[i] = Z[2 * i];
+}
+
+// ---------------------------------------------------------------------------
+// Column pass (forward).  CTA = C consecutive columns q0 .. q0 + C - 1 of the
+// R-wide matrix view; rows t <= a.  src may differ from dst (the product
+// reads its operand and writes the output buffer); elements of src at
+// positions >= n_src are zero (the operand's zero extension).
+// ---------------------------------------------------------------------------
+template <class F>
+__global__ void __launch_bounds__(512)
+k_col_fwd(const typename F::T* src, uint64_t n_src, typename F::T* dst,
+          typename F::T* __restrict__ E, int lr, uint64_t a, uint64_t b, int c,
+          int clog, uint32_t q_begin, uint32_t q_end,
+          RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  load_roots<F>(&s_rt, rt);
+  const uint32_t C = 1u << clog;
+  const uint32_t N = 1u << c;
+  T* Z = reinterpret_cast<T*>(smem_raw);
+  T* W = Z + ((size_t)N << clog);
+  build_base_tables<F>(W, nullptr, c, s_rt);
+  const uint64_t R = 1ull << lr;
+  const uint32_t q0 = q_begin + blockIdx.x * C;
+  const uint32_t total = N << clog;
+  // rows produced: a, plus row a (long columns' last value or E_q) if b > 0
+  const uint32_t rows = (uint32_t)(a + (b > 0 ? 1 : 0));
+  for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const uint32_t t = i >> clog;
+    const uint64_t q = q0 + (i & (C - 1));
+    T v = 0;
+    if (q < q_end && t < rows) {
+      const uint64_t pos = q + (uint64_t)t * R;
+      if (pos < n_src) v = src[pos];
+    }
+    Z[i] = v;
+  }
+  __syncthreads();
+  fwd_pruned<F>(Z, clog, clog, c, rows, ColTw<F>{W, nullptr});
+  for (uint32_t i = threadIdx.x; i < (rows << clog); i += blockDim.x) {
+    const uint32_t t = i >> clog;
+    const uint64_t q = q0 + (i & (C - 1));
+    if (q >= q_end) continue;
+    if (t < a)
+      dst[q + (uint64_t)t * R] = Z[i];
+    else if (q < b)
+      dst[q + a * R] = Z[i];
+    else
+      E[q] = Z[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row pass (forward), persistent over rows.  Rows rho < a are full blocks of
+// the network; if b > 0 the last row rho = a is processed first (by CTA 0)
+// from the long columns' last entries (q < b) and E (q >= b), and only its
+// first b outputs are computed and stored.
+// ---------------------------------------------------------------------------
+template <class F>
+__global__ void __launch_bounds__(512)
+k_row_fwd(typename F::T* X, const typename F::T* __restrict__ E, int lr,
+          uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  load_roots<F>(&s_rt, rt);
+  const uint32_t R = 1u << lr;
+  T* Z = reinterpret_cast<T*>(smem_raw);
+  T* W = Z + R;
+  T* L = W + R / 2;
+  build_base_tables<F>(W, nullptr, lr, s_rt);
+  const uint64_t nrows = a + (b > 0 ? 1 : 0);
+  for (uint64_t it = blockIdx.x; it < nrows; it += gridDim.x) {
+    const uint64_t rho = (b > 0) ? (it == 0 ? a : it - 1) : it;
+    const bool last = rho == a;
+    T* row = X + rho * R;
+    for (uint32_t q = threadIdx.x; q < R; q += blockDim.x)
+      Z[q] = (!last || q < b) ? row[q] : E[q];
+    __syncthreads();
+    RowTw<F> tw{W, nullptr, L, &s_rt, rho, lr};
+    const uint32_t nout = last ? (uint32_t)b : R;
+    fwd_pruned<F>(Z, 0, 0, lr, nout, tw);
+    for (uint32_t q = threadIdx.x; q < nout; q += blockDim.x) row[q] = Z[q];
+    __syncthreads();
+  }
+}
+
+// Row pass (inverse) over the full rows rho < a.
+template <class F>
+__global__ void __launch_bounds__(512)
+k_row_inv(typename F::T* X, int lr, uint64_t a, RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  load_roots<F>(&s_rt, rt);
+  const uint32_t R = 1u << lr;
+  T* Z = reinterpret_cast<T*>(smem_raw);
+  T* W = Z + R;
+  T* Wih = W + R / 2;
+  T* L = Wih + R / 2;
+  build_base_tables<F>(W, Wih, lr, s_rt);
+  for (uint64_t rho = blockIdx.x; rho < a; rho += gridDim.x) {
+    T* row = X + rho * R;
+    for (uint32_t q = threadIdx.x; q < R; q += blockDim.x) Z[q] = row[q];
+    __syncthreads();
+    RowTw<F> tw{W, Wih, L, &s_rt, rho, lr};
+    inv_full<F>(Z, 0, 0, lr, tw);
+    for (uint32_t q = threadIdx.x; q < R; q += blockDim.x) row[q] = Z[q];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass (inverse) over columns [q_begin, q_end), all of length m
+// (m = a for short columns, a + 1 for long ones).  With want_E the kernel
+// also evaluates E_q = C_q(omega_a) by a parallel Horner rule (short
+// columns), omega_a given in twiddle form.
+// ---------------------------------------------------------------------------
+template <class F>
+__global__ void __launch_bounds__(512)
+k_col_inv(typename F::T* X, typename F::T* __restrict__ E, int lr, uint32_t m,
+          int c, int clog, uint32_t q_begin, uint32_t q_end, int want_E,
+          typename F::T omega_a_tw, RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  load_roots<F>(&s_rt, rt);
+  const uint32_t C = 1u << clog;
+  const uint32_t N = 1u << c;
+  T* Z = reinterpret_cast<T*>(smem_raw);
+  T* W = Z + ((size_t)N << clog);
+  T* Wih = W + (N > 1 ? N / 2 : 1);
+  build_base_tables<F>(W, Wih, c, s_rt);
+  const uint64_t R = 1ull << lr;
+  const uint32_t q0 = q_begin + blockIdx.x * C;
+  const uint32_t total = N << clog;
+  for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
+    const uint32_t t = i >> clog;
+    const uint64_t q = q0 + (i & (C - 1));
+    Z[i] = (q < q_end && t < m) ? X[q + (uint64_t)t * R] : T(0);
+  }
+  __syncthreads();
+  inv_block<F>(Z, clog, clog, c, m, ColTw<F>{W, Wih});
+  for (uint32_t i = threadIdx.x; i < (m << clog); i += blockDim.x) {
+    const uint32_t t = i >> clog;
+    const uint64_t q = q0 + (i & (C - 1));
+    if (q < q_end) X[q + (uint64_t)t * R] = Z[i];
+  }
+  if (want_E) {
+    // threads per column: blockDim / C; each takes a contiguous chunk of rows
+    const uint32_t tpc = blockDim.x >> clog;
+    const uint32_t cc = threadIdx.x & (C - 1);
+    const uint32_t k = threadIdx.x >> clog;
+    const uint32_t chunk = (m + tpc - 1) / tpc;
+    const uint32_t t0 = k * chunk;
+    uint32_t t1 = t0 + chunk;
+    if (t1 > m) t1 = m;
+    T acc = 0;
+    for (uint32_t t = t1; t > t0; --t)
+      acc = F::add(F::mul_tw(acc, omega_a_tw), Z[((t - 1) << clog) + cc]);
+    if (t0 < m) acc = F::mul_tw(acc, pow_tw<F>(omega_a_tw, t0, s_rt.one_tw));
+    else acc = 0;
+    __syncthreads();
+    T* part = W;  // reuse the table area (>= blockDim entries)
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < C) {
+      T s = 0;
+      for (uint32_t kk = 0; kk < tpc; ++kk)
+        s = F::add(s, part[(kk << clog) + threadIdx.x]);
+      const uint64_t q = q0 + threadIdx.x;
+      if (q < q_end) E[q] = s;
+    }
+  }
+}
+
+// Last row inverse (one CTA): block a of the network with outputs known at
+// q < b and inputs known at q >= b (E_q = C_q(omega_a)).  Writes the b
+// recovered inputs (the long columns' last transform values).
+template <class F>
+__global__ void __launch_bounds__(512)
+k_lastrow_inv(typename F::T* X, const typename F::T* __restrict__ E, int lr,
+              uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  load_roots<F>(&s_rt, rt);
+  const uint32_t R = 1u << lr;
+  T* Z = reinterpret_cast<T*>(smem_raw);
+  T* W = Z + R;
+  T* Wih = W + R / 2;
+  T* L = Wih + R / 2;
+  build_base_tables<F>(W, Wih, lr, s_rt);
+  T* row = X + a * R;
+  for (uint32_t q = threadIdx.x; q < R; q += blockDim.x)
+    Z[q] = q < b ? row[q] : E[q];
+  __syncthreads();
+  RowTw<F> tw{W, Wih, L, &s_rt, a, lr};
+  inv_block<F>(Z, 0, 0, lr, (uint32_t)b, tw);
+  for (uint32_t q = threadIdx.x; q < b; q += blockDim.x) row[q] = Z[q];
+}
+
+// ---------------------------------------------------------------------------
+// Fused product row pass, persistent over rows.  For a full row rho < a the
+// two column-transformed operands (A' in out, B' in work) are interleaved as
+// a two-column tile, both run the forward row network, are multiplied
+// pointwise (C^_s = A^_s B^_s), and the product runs the inverse row network;
+// the result goes back to out.  The last row (rho = a, first b outputs) only
+// gets the forward half and the pointwise product: its inverse needs the
+// inverse column pass first.
+// ---------------------------------------------------------------------------
+template <class F>
+__global__ void __launch_bounds__(512)
+k_row_mul(typename F::T* out, const typename F::T* __restrict__ work,
+          const typename F::T* __restrict__ EA,
+          const typename F::T* __restrict__ EB, int lr, uint64_t a, uint64_t b,
+          RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  load_roots<F>(&s_rt, rt);
+  const uint32_t R = 1u << lr;
+  T* Z = reinterpret_cast<T*>(smem_raw);  // 2R
+  T* W = Z + 2 * R;
+  T* Wih = W + R / 2;
+  T* L = Wih + R / 2;
+  build_base_tables<F>(W, Wih, lr, s_rt);
+  const uint64_t nrows = a + (b > 0 ? 1 : 0);
+  for (uint64_t it = blockIdx.x; it < nrows; it += gridDim.x) {
+    const uint64_t rho = (b > 0) ? (it == 0 ? a : it - 1) : it;
+    const bool last = rho == a;
+    T* orow = out + rho * R;
+    const T* wrow = work + rho * R;
+    for (uint32_t q = threadIdx.x; q < R; q += blockDim.x) {
+      const bool mem = !last || q < b;
+      Z[2 * q] = mem ? orow[q] : EA[q];
+      Z[2 * q + 1] = mem ? wrow[q] : EB[q];
+    }
+    __syncthreads();
+    RowTw<F> tw{W, Wih, L, &s_rt, rho, lr};
+    const uint32_t nout = last ? (uint32_t)b : R;
+    fwd_pruned<F>(Z, 1, 1, lr, nout, tw);
+    for (uint32_t q = threadIdx.x; q < nout; q += blockDim.x)
+      Z[2 * q] = F::mul_data(Z[2 * q], Z[2 * q + 1]);
+    __syncthreads();
+    if (!last) inv_full<F>(Z, 0, 1, lr, tw);
+    for (uint32_t q = threadIdx.x; q < nout; q += blockDim.x)
+      orow[q] = Z[2 * q];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+template <class F>
+static size_t smem_small(int l, bool inv) {
+  const size_t N = 1ull << l;
+  return (N + 2 * (N > 1 ? N / 2 : 1)) * sizeof(typename F::T);
+}
+template <class F>
+static size_t smem_small_mul(int l) {
+  const size_t N = 1ull << l;
+  return (2 * N + 2 * (N > 1 ? N / 2 : 1)) * sizeof(typename F::T);
+}
+template <class F>
+static size_t smem_col(int c, int clog, bool inv) {
+  const size_t N = 1ull << c;
+  size_t tab = inv ? 2 * (N > 1 ? N / 2 : 1) : (N > 1 ? N / 2 : 1);
+  if (inv && tab < 512) tab = 512;  // the Horner reduction reuses it
+  return ((N << clog) + tab) * sizeof(typename F::T);
+}
+template <class F>
+static size_t smem_row(int lr, int kind) {
+  const size_t R = 1ull << lr;
+  switch (kind) {
+    case 0: return (R + R / 2 + R / 2) * sizeof(typename F::T);      // fwd
+    case 1: return (R + 3 * (R / 2)) * sizeof(typename F::T);        // inv
+    default: return (2 * R + 3 * (R / 2)) * sizeof(typename F::T);   // mul
+  }
+}
+
+// Allow each kernel the device's opt-in shared memory minus its own static
+// shared memory (the per-CTA copy of the root table).
+template <class F>
+static cudaError_t set_smem(const void* fn, size_t optin) {
+  cudaFuncAttributes at;
+  cudaError_t e = cudaFuncGetAttributes(&at, fn);
+  if (e != cudaSuccess) return e;
+  const size_t dyn = optin > at.sharedSizeBytes ? optin - at.sharedSizeBytes : 0;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)dyn);
+}
+
+// Launch with the optional hook around it (H and s in scope).
+#define TFT_LAUNCH(kind, ...)                        \
+  do {                                               \
+    if (H) H->before(H->user, (kind), s);            \
+    __VA_ARGS__;                                     \
+    if (H) H->after(H->user, (kind), s);             \
+  } while (0)
+
+template <class F>
+struct Launch {
+  using T = typename F::T;
+  using RT = RootTable<T>;
+
+  static cudaError_t prepare(size_t mx) {
+    cudaError_t e;
+    if ((e = set_smem<F>((const void*)k_small<F, false>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_small<F, true>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_small_mul<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_col_fwd<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_col_inv<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_fwd<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_inv<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_mul<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_lastrow_inv<F>, mx))) return e;
+    return cudaSuccess;
+  }
+
+  static cudaError_t forward(T* x, uint64_t n, const Plan& P, T* E,
+                             const RT& rt, int nsm, cudaStream_t s,
+                             const LaunchHook* H) {
+    if (P.small) {
+      TFT_LAUNCH(K_SMALL, k_small<F, false><<<1, 512,
+                                              smem_small<F>(P.l, false), s>>>(
+                              x, (uint32_t)n, P.l, rt));
+      return cudaGetLastError();
+    }
+    const uint32_t R = 1u << P.lr;
+    const uint32_t C = 1u << P.clog;
+    TFT_LAUNCH(K_COL_FWD,
+               k_col_fwd<F><<<(R + C - 1) / C, 512,
+                              smem_col<F>(P.c, P.clog, false), s>>>(
+                   x, n, x, E, P.lr, P.a, P.b, P.c, P.clog, 0, R, rt));
+    const uint64_t rows = P.a + (P.b ? 1 : 0);
+    const uint32_t grid = (uint32_t)(rows < (uint64_t)nsm * P.row_ctas_per_sm
+                                         ? rows
+                                         : (uint64_t)nsm * P.row_ctas_per_sm);
+    TFT_LAUNCH(K_ROW_FWD, k_row_fwd<F><<<grid, 512, smem_row<F>(P.lr, 0), s>>>(
+                              x, E, P.lr, P.a, P.b, rt));
+    return cudaGetLastError();
+  }
+
+  static cudaError_t inverse_tail(T* x, const Plan& P, T* E, T omega_a_tw,
+                                  const RT& rt, cudaStream_t s,
+                                  const LaunchHook* H) {
+    const uint32_t R = 1u << P.lr;
+    const uint32_t C = 1u << P.clog;
+    // short columns q in [b, R): length a, and E_q = C_q(omega_a)
+    if (P.a > 0 && P.b < R) {
+      const uint32_t qb = (uint32_t)P.b;
+      TFT_LAUNCH(K_COL_INV,
+                 k_col_inv<F><<<(R - qb + C - 1) / C, 512,
+                                smem_col<F>(P.c, P.clog, true), s>>>(
+                     x, E, P.lr, (uint32_t)P.a, P.c, P.clog, qb, R,
+                     P.b > 0 ? 1 : 0, omega_a_tw, rt));
+    }
+    if (P.b > 0) {
+      TFT_LAUNCH(K_LASTROW_INV,
+                 k_lastrow_inv<F><<<1, 512, smem_row<F>(P.lr, 1), s>>>(
+                     x, E, P.lr, P.a, P.b, rt));
+      const uint32_t qe = (uint32_t)P.b;
+      TFT_LAUNCH(K_COL_INV,
+                 k_col_inv<F><<<(qe + C - 1) / C, 512,
+                                smem_col<F>(P.c, P.clog, true), s>>>(
+                     x, E, P.lr, (uint32_t)(P.a + 1), P.c, P.clog, 0, qe, 0,
+                     omega_a_tw, rt));
+    }
+    return cudaGetLastError();
+  }
+
+  static cudaError_t inverse(T* x, uint64_t n, const Plan& P, T* E,
+                             T omega_a_tw, const RT& rt, int nsm,
+                             cudaStream_t s, const LaunchHook* H) {
+    if (P.small) {
+      TFT_LAUNCH(K_SMALL, k_small<F, true><<<1, 512, smem_small<F>(P.l, true),
+                                             s>>>(x, (uint32_t)n, P.l, rt));
+      return cudaGetLastError();
+    }
+    if (P.a > 0) {
+      const uint32_t grid = (uint32_t)(P.a < (uint64_t)nsm * P.row_ctas_per_sm
+                                           ? P.a
+                                           : (uint64_t)nsm * P.row_ctas_per_sm);
+      TFT_LAUNCH(K_ROW_INV,
+                 k_row_inv<F><<<grid, 512, smem_row<F>(P.lr, 1), s>>>(
+                     x, P.lr, P.a, rt));
+    }
+    return inverse_tail(x, P, E, omega_a_tw, rt, s, H);
+  }
+
+  static cudaError_t polymul(const T* a, uint64_t na, const T* b, uint64_t nb,
+                             T* out, const Plan& P, T* work, T* EA, T* EB,
+                             T omega_a_tw, const RT& rt, int nsm,
+                             cudaStream_t s, const LaunchHook* H) {
+    if (P.small) {
+      TFT_LAUNCH(K_SMALL_MUL,
+                 k_small_mul<F><<<1, 512, smem_small_mul<F>(P.l), s>>>(
+                     a, (uint32_t)na, b, (uint32_t)nb, out, P.l, rt));
+      return cudaGetLastError();
+    }
+    const uint32_t R = 1u << P.lr;
+    const uint32_t C = 1u << P.clog;
+    const size_t sc = smem_col<F>(P.c, P.clog, false);
+    TFT_LAUNCH(K_COL_FWD, k_col_fwd<F><<<(R + C - 1) / C, 512, sc, s>>>(
+                              a, na, out, EA, P.lr, P.a, P.b, P.c, P.clog, 0,
+                              R, rt));
+    TFT_LAUNCH(K_COL_FWD, k_col_fwd<F><<<(R + C - 1) / C, 512, sc, s>>>(
+                              b, nb, work, EB, P.lr, P.a, P.b, P.c, P.clog, 0,
+                              R, rt));
+    const uint64_t rows = P.a + (P.b ? 1 : 0);
+    const uint32_t grid = (uint32_t)(rows < (uint64_t)nsm * P.row_ctas_per_sm
+                                         ? rows
+                                         : (uint64_t)nsm * P.row_ctas_per_sm);
+    TFT_LAUNCH(K_ROW_MUL, k_row_mul<F><<<grid, 512, smem_row<F>(P.lr, 2), s>>>(
+                              out, work, EA, EB, P.lr, P.a, P.b, rt));
+    return inverse_tail(out, P, EA, omega_a_tw, rt, s, H);
+  }
+};
+
+// Shared-memory bytes of each kernel for a plan (used by the planner).
+template <class F>
+static PlanSmem smem_of(const Plan& P) {
+  PlanSmem m{};
+  if (P.small) {
+    m.col = smem_small<F>(P.l, true);
+    m.row = smem_small_mul<F>(P.l);
+    return m;
+  }
+  m.col = smem_col<F>(P.c, P.clog, true);
+  m.row = smem_row<F>(P.lr, 2);
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// Prime dispatch
+// ---------------------------------------------------------------------------
+#define TFT_DISPATCH(prime, CALL)                          \
+  switch (prime) {                                         \
+    case 0: { using F = P998; CALL; }                      \
+    case 1: { using F = P2013; CALL; }                     \
+    case 2: { using F = Goldilocks; CALL; }                \
+    default: return cudaErrorInvalidValue;                 \
+  }
+
+cudaError_t prepare_kernels(int prime, size_t optin_smem) {
+  TFT_DISPATCH(prime, return Launch<F>::prepare(optin_smem));
+}
+
+cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
+                           void* E, const void* rt, int nsm, cudaStream_t s,
+                           const LaunchHook* hook) {
+  TFT_DISPATCH(prime, return Launch<F>::forward(
+                          (typename F::T*)x, n, P, (typename F::T*)E,
+                          *(const RootTable<typename F::T>*)rt, nsm, s, hook));
+}
+
+cudaError_t launch_inverse(int prime, void* x, uint64_t n, const Plan& P,
+                           void* E, uint64_t omega_a_tw, const void* rt,
+                           int nsm, cudaStream_t s, const LaunchHook* hook) {
+  TFT_DISPATCH(prime,
+               return Launch<F>::inverse(
+                   (typename F::T*)x, n, P, (typename F::T*)E,
+                   (typename F::T)omega_a_tw,
+                   *(const RootTable<typename F::T>*)rt, nsm, s, hook));
+}
+
+cudaError_t launch_polymul(int prime, const void* a, uint64_t na,
+                           const void* b, uint64_t nb, void* out,
+                           const Plan& P, void* work, void* EA, void* EB,
+                           uint64_t omega_a_tw, const void* rt, int nsm,
+                           cudaStream_t s, const LaunchHook* hook) {
+  TFT_DISPATCH(prime,
+               return Launch<F>::polymul(
+                   (const typename F::T*)a, na, (const typename F::T*)b, nb,
+                   (typename F::T*)out, P, (typename F::T*)work,
+                   (typename F::T*)EA, (typename F::T*)EB,
+                   (typename F::T)omega_a_tw,
+                   *(const RootTable<typename F::T>*)rt, nsm, s, hook));
+}
+
+PlanSmem plan_smem(int prime, const Plan& P) {
+  switch (prime) {
+    case 0: return smem_of<P998>(P);
+    case 1: return smem_of<P2013>(P);
+    default: return smem_of<Goldilocks>(P);
+  }
+}
+
+}  // namespace tftgb

@@ -1,0 +1,66 @@
+// Internal interface between the C-ABI layer (api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace tftgb {
+
+// Kernel kinds, for launch counting and per-kernel timing (the numbering is
+// part of the C ABI: tft_kernel_name / tft_profile_read).
+enum KernelKind {
+  K_SMALL = 0,
+  K_SMALL_MUL = 1,
+  K_COL_FWD = 2,
+  K_ROW_FWD = 3,
+  K_ROW_INV = 4,
+  K_COL_INV = 5,
+  K_LASTROW_INV = 6,
+  K_ROW_MUL = 7,
+  K_NUM_KINDS = 8
+};
+
+// Called around every kernel launch (may be null).
+struct LaunchHook {
+  void (*before)(void* user, int kind, cudaStream_t s);
+  void (*after)(void* user, int kind, cudaStream_t s);
+  void* user;
+};
+
+// Execution plan for one transform length.
+//   small = 1: the whole transform in one CTA, padded in shared memory to 2^l.
+//   small = 0: n = a 2^lr + b; columns padded to 2^c in shared memory, C =
+//              2^clog columns per CTA; row kernels persistent with
+//              row_ctas_per_sm CTAs per SM.
+struct Plan {
+  int small;
+  int l;
+  int lr;
+  int c;
+  int clog;
+  uint64_t a;
+  uint64_t b;
+  int row_ctas_per_sm;
+};
+
+struct PlanSmem {
+  size_t col;
+  size_t row;
+};
+
+cudaError_t prepare_kernels(int prime, size_t optin_smem);
+PlanSmem plan_smem(int prime, const Plan& P);
+
+cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
+                           void* E, const void* rt, int nsm, cudaStream_t s,
+                           const LaunchHook* hook);
+cudaError_t launch_inverse(int prime, void* x, uint64_t n, const Plan& P,
+                           void* E, uint64_t omega_a_tw, const void* rt,
+                           int nsm, cudaStream_t s, const LaunchHook* hook);
+cudaError_t launch_polymul(int prime, const void* a, uint64_t na,
+                           const void* b, uint64_t nb, void* out,
+                           const Plan& P, void* work, void* EA, void* EB,
+                           uint64_t omega_a_tw, const void* rt, int nsm,
+                           cudaStream_t s, const LaunchHook* hook);
+
+}  // namespace tftgb

@@ -1,0 +1,294 @@
+"""Python binding of the C ABI in include/tft.h (argument marshalling only).
+
+Every function keeps the C name and forwards to the in-tree shared library
+``_lib/libtft_gb300.so``; no step of any transform runs in Python.  Device
+buffers are torch CUDA tensors (any dtype whose element size is the prime's:
+4 bytes for 998244353 and 2013265921, 8 bytes for 2^64 - 2^32 + 1; the bits
+are the canonical residues).  Host-buffer calls take numpy arrays or CPU
+tensors.  If the library is missing the import of this module still works,
+but every call raises ``RuntimeError`` -- there is no fallback.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libtft_gb300.so")
+
+TFT_P998244353 = 0
+TFT_P2013265921 = 1
+TFT_PGOLDILOCKS = 2
+PRIME_IDS = {"p998244353": 0, "p2013265921": 1, "goldilocks": 2,
+             998244353: 0, 2013265921: 1, 2**64 - 2**32 + 1: 2}
+MODULI = {0: 998244353, 1: 2013265921, 2: 2**64 - 2**32 + 1}
+TWO_ADICITY = {0: 23, 1: 27, 2: 32}
+
+TFT_OK, TFT_EINVAL, TFT_ERANGE, TFT_ENOMEM, TFT_ECUDA, TFT_ETIMEOUT = range(6)
+TFT_CTX_HOST_STAGING = 1
+
+_lib = None
+
+
+class TFTError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"CUDA library not built: {LIB_PATH} is missing "
+            "(run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    u64, u32, i32, vp = (ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                         ctypes.c_void_p)
+    sig = {
+        "tft_ctx_create": (i32, [i32, i32, u64, u32,
+                                 ctypes.POINTER(ctypes.c_void_p)]),
+        "tft_ctx_destroy": (i32, [vp]),
+        "tft_forward": (i32, [vp, vp, u64, u32, vp]),
+        "tft_inverse": (i32, [vp, vp, u64, u32, vp]),
+        "tft_polymul": (i32, [vp, vp, u64, vp, u64, vp, vp]),
+        "tft_forward_host": (i32, [vp, vp, u64, u32, vp]),
+        "tft_inverse_host": (i32, [vp, vp, u64, u32, vp]),
+        "tft_polymul_host": (i32, [vp, vp, u64, vp, u64, vp, vp]),
+        "tft_footprint": (i32, [i32, u64, u32, i32,
+                                ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+        "tft_describe_plan": (i32, [i32, u64,
+                                    ctypes.POINTER(ctypes.c_int64)]),
+        "tft_element_bytes": (u32, [i32]),
+        "tft_last_error": (i32, [vp]),
+        "tft_status_string": (ctypes.c_char_p, [i32]),
+        "tft_last_cuda_error": (ctypes.c_char_p, []),
+        "tft_profile_enable": (i32, [vp, i32]),
+        "tft_profile_read": (i32, [vp, ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(u64)]),
+        "tft_kernel_name": (ctypes.c_char_p, [i32]),
+        "tft_launch_count": (u64, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names declared in include/tft.h that the loaded library exports."""
+    L = load()
+    return [n for n in _header_functions() if hasattr(L, n)]
+
+
+def _header_functions():
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "tft.h")
+    text = open(hdr).read()
+    return re.findall(
+        r"^\s*(?:tft_status|uint32_t|uint64_t|const char\*)\s+(tft_\w+)\(",
+        text, flags=re.M)
+
+
+def status_string(s):
+    try:
+        return load().tft_status_string(int(s)).decode()
+    except RuntimeError:
+        return str(s)
+
+
+def _check(st, what):
+    if st != TFT_OK:
+        if st == TFT_ECUDA:
+            what = f"{what} [{load().tft_last_cuda_error().decode()}]"
+        raise TFTError(st, what)
+
+
+def prime_id(prime):
+    if isinstance(prime, int) and prime in (0, 1, 2):
+        return prime
+    return PRIME_IDS[prime]
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev_ptr(t, elem_bytes, what):
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if t.element_size() != elem_bytes:
+        raise ValueError(f"{what}: element size {t.element_size()} != "
+                         f"{elem_bytes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(arr, elem_bytes, what):
+    if hasattr(arr, "data_ptr"):  # torch CPU tensor
+        if arr.is_cuda or arr.element_size() != elem_bytes or \
+                not arr.is_contiguous():
+            raise ValueError(f"{what}: need a contiguous CPU tensor of "
+                             f"{elem_bytes}-byte elements")
+        return ctypes.c_void_p(arr.data_ptr()), arr.numel()
+    import numpy as np
+    if not isinstance(arr, np.ndarray) or arr.itemsize != elem_bytes or \
+            not arr.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{what}: need a C-contiguous numpy array of "
+                         f"{elem_bytes}-byte elements")
+    return ctypes.c_void_p(arr.ctypes.data), arr.size
+
+
+class Context:
+    """Owns a ``tft_ctx`` (root table, fixed scratch, product work buffer)."""
+
+    def __init__(self, prime, device=0, max_len=1 << 20, host_staging=False):
+        L = load()
+        self.prime = prime_id(prime)
+        self.device = device
+        self.max_len = int(max_len)
+        self.elem_bytes = int(L.tft_element_bytes(self.prime))
+        h = ctypes.c_void_p()
+        flags = TFT_CTX_HOST_STAGING if host_staging else 0
+        _check(L.tft_ctx_create(self.prime, device, self.max_len, flags,
+                                ctypes.byref(h)), "tft_ctx_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("context destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().tft_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def _default_k(n):
+    return max(0, (int(n) - 1).bit_length())
+
+
+def tft_forward(ctx, x, k=None, stream=None):
+    """In-place forward TFT of the CUDA tensor ``x`` (Algorithm 1)."""
+    n = x.numel()
+    k = _default_k(n) if k is None else int(k)
+    _check(load().tft_forward(ctx.handle, _dev_ptr(x, ctx.elem_bytes, "x"),
+                              n, k, _stream_handle(stream)), "tft_forward")
+    return x
+
+
+def tft_inverse(ctx, X, k=None, stream=None):
+    """In-place inverse TFT of the CUDA tensor ``X`` (Algorithm 2)."""
+    n = X.numel()
+    k = _default_k(n) if k is None else int(k)
+    _check(load().tft_inverse(ctx.handle, _dev_ptr(X, ctx.elem_bytes, "X"),
+                              n, k, _stream_handle(stream)), "tft_inverse")
+    return X
+
+
+def tft_polymul(ctx, a, b, out, stream=None):
+    """out = a * b mod p for CUDA tensors (len(out) = len(a) + len(b) - 1)."""
+    if out.numel() != a.numel() + b.numel() - 1:
+        raise ValueError("out must have len(a) + len(b) - 1 elements")
+    _check(load().tft_polymul(ctx.handle, _dev_ptr(a, ctx.elem_bytes, "a"),
+                              a.numel(), _dev_ptr(b, ctx.elem_bytes, "b"),
+                              b.numel(), _dev_ptr(out, ctx.elem_bytes, "out"),
+                              _stream_handle(stream)), "tft_polymul")
+    return out
+
+
+def tft_forward_host(ctx, x, k=None, stream=None):
+    ptr, n = _host_ptr(x, ctx.elem_bytes, "x")
+    k = _default_k(n) if k is None else int(k)
+    _check(load().tft_forward_host(ctx.handle, ptr, n, k,
+                                   _stream_handle(stream)), "tft_forward_host")
+    return x
+
+
+def tft_inverse_host(ctx, X, k=None, stream=None):
+    ptr, n = _host_ptr(X, ctx.elem_bytes, "X")
+    k = _default_k(n) if k is None else int(k)
+    _check(load().tft_inverse_host(ctx.handle, ptr, n, k,
+                                   _stream_handle(stream)), "tft_inverse_host")
+    return X
+
+
+def tft_polymul_host(ctx, a, b, out, stream=None):
+    pa, na = _host_ptr(a, ctx.elem_bytes, "a")
+    pb, nb = _host_ptr(b, ctx.elem_bytes, "b")
+    po, no = _host_ptr(out, ctx.elem_bytes, "out")
+    if no != na + nb - 1:
+        raise ValueError("out must have len(a) + len(b) - 1 elements")
+    _check(load().tft_polymul_host(ctx.handle, pa, na, pb, nb, po,
+                                   _stream_handle(stream)), "tft_polymul_host")
+    return out
+
+
+def tft_footprint(prime, n, k=0, op=0):
+    """(inplace_bytes, padded_bytes) of a transform (op=0) or product (op=1)."""
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().tft_footprint(prime_id(prime), int(n), int(k), int(op),
+                                ctypes.byref(a), ctypes.byref(b)),
+           "tft_footprint")
+    return a.value, b.value
+
+
+def tft_describe_plan(prime, n):
+    out = (ctypes.c_int64 * 8)()
+    _check(load().tft_describe_plan(prime_id(prime), int(n), out),
+           "tft_describe_plan")
+    keys = ("small", "l", "lr", "c", "clog", "a", "b", "row_ctas_per_sm")
+    return dict(zip(keys, [int(v) for v in out]))
+
+
+def tft_last_error(ctx):
+    return int(load().tft_last_error(ctx.handle))
+
+
+NUM_KERNEL_KINDS = 8
+
+
+def kernel_name(kind):
+    return load().tft_kernel_name(int(kind)).decode()
+
+
+def tft_profile_enable(ctx, enable=True):
+    _check(load().tft_profile_enable(ctx.handle, 1 if enable else 0),
+           "tft_profile_enable")
+
+
+def tft_profile_read(ctx):
+    """{kernel name: (total ms, timed launches)} since the last enable."""
+    ms = (ctypes.c_double * NUM_KERNEL_KINDS)()
+    cnt = (ctypes.c_uint64 * NUM_KERNEL_KINDS)()
+    _check(load().tft_profile_read(ctx.handle, ms, cnt), "tft_profile_read")
+    return {kernel_name(k): (ms[k], int(cnt[k]))
+            for k in range(NUM_KERNEL_KINDS) if cnt[k]}
+
+
+def tft_launch_count(ctx):
+    return int(load().tft_launch_count(ctx.handle))

@@ -1,0 +1,99 @@
+"""CPU-only checks of the C library: it builds, loads, exports every symbol
+that include/tft.h declares, and its host-side logic (planning, footprint,
+argument checks that need no device) behaves.  No kernel is launched."""
+
+import ctypes
+
+import pytest
+
+from paper_1001_5272_gb300 import build as B
+from paper_1001_5272_gb300 import tft
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def test_exports_every_declared_symbol():
+    declared = tft._header_functions()
+    assert len(declared) >= 13
+    L = tft.load()
+    missing = [n for n in declared if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    assert tft.status_string(0) == "ok"
+    assert tft.status_string(1) == "invalid argument"
+    assert tft.status_string(5) == "device wait timed out"
+
+
+@pytest.mark.parametrize("pid", [0, 1, 2])
+def test_plan_invariants(pid):
+    w = 8 if pid == 2 else 4
+    for e in range(0, 26 if w == 8 else 28):
+        for n in {(1 << e) - 1, 1 << e, (1 << e) + 1, 3 << max(0, e - 2),
+                  (1 << e) + 12345}:
+            if n < 1:
+                continue
+            try:
+                P = tft.tft_describe_plan(pid, n)
+            except tft.TFTError as err:
+                assert err.status == tft.TFT_ERANGE
+                assert n > ((1 << 25) if w == 8 else (1 << 27))
+                continue
+            if P["small"]:
+                assert n <= 1 << P["l"] and (P["l"] == 0 or n > 1 << (P["l"] - 1))
+                continue
+            R = 1 << P["lr"]
+            assert P["a"] * R + P["b"] == n and 0 <= P["b"] < R
+            assert P["a"] >= 1
+            rows = P["a"] + (1 if P["b"] else 0)
+            assert rows <= 1 << P["c"]
+            assert (1 << P["clog"]) <= R
+            assert 1 <= P["row_ctas_per_sm"] <= 4
+
+
+def test_footprint_against_padded():
+    # n = 2^24 + 2^20 + 12345 words of 8 bytes plus one R-word scratch,
+    # against a padded 2^25 buffer.
+    n = 2**24 + 2**20 + 12345
+    inplace, padded = tft.tft_footprint(2, n, 25, 0)
+    P = tft.tft_describe_plan(2, n)
+    assert inplace == (n + (1 << P["lr"])) * 8
+    assert padded == (1 << 25) * 8
+    assert inplace < 0.54 * padded
+    # product r = 8,000,000: out + work (+ two R-word scratches) vs 2 x 2^23
+    inplace, padded = tft.tft_footprint(2, 8_000_000, 0, 1)
+    P = tft.tft_describe_plan(2, 8_000_000)
+    assert inplace == (2 * 8_000_000 + 2 * (1 << P["lr"])) * 8
+    assert padded == 2 * (1 << 23) * 8
+    with pytest.raises(tft.TFTError):
+        tft.tft_footprint(2, 0, 0, 0)
+    with pytest.raises(tft.TFTError):
+        tft.tft_footprint(0, 1025, 10, 0)         # n > 2^k
+
+
+def test_null_arguments_rejected_without_a_device():
+    L = tft.load()
+    assert L.tft_forward(None, ctypes.c_void_p(16), 4, 2, None) == tft.TFT_EINVAL
+    assert L.tft_ctx_destroy(None) == tft.TFT_EINVAL
+    h = ctypes.c_void_p()
+    assert L.tft_ctx_create(7, 0, 16, 0, ctypes.byref(h)) == tft.TFT_EINVAL
+    assert L.tft_ctx_create(0, 0, 0, 0, ctypes.byref(h)) == tft.TFT_EINVAL
+    assert L.tft_ctx_create(2, 0, (1 << 25) + 1, 0,
+                            ctypes.byref(h)) == tft.TFT_ERANGE
+    assert L.tft_element_bytes(0) == 4 and L.tft_element_bytes(2) == 8
+    assert L.tft_element_bytes(9) == 0
+
+
+def test_context_creation_without_gpu_fails_cleanly():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    L = tft.load()
+    h = ctypes.c_void_p()
+    st = L.tft_ctx_create(2, 0, 1024, 0, ctypes.byref(h))
+    assert st in (tft.TFT_ECUDA, tft.TFT_EINVAL)
+    assert not h.value
