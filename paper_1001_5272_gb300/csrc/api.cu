@@ -201,6 +201,12 @@ void build_root_table(tft_ctx* c) {
     wi[j] = powm(v, pr.p - 2, pr.p);
   }
   const uint64_t half = (pr.p + 1) / 2;
+  // 16-point network twiddles omega_{2k} = omega_s at s = 2k, k < 8
+  uint64_t c16[8], c16i[8];
+  for (int k = 0; k < 8; ++k) {
+    c16[k] = omega_s(pr, 2 * k);
+    c16i[k] = mulm(powm(c16[k], pr.p - 2, pr.p), half, pr.p);
+  }
   if (pr.w == 8) {
     RootTable<uint64_t> t;
     for (int j = 0; j <= 32; ++j) {
@@ -209,6 +215,10 @@ void build_root_table(tft_ctx* c) {
     }
     t.half_tw = to_tw(pr, half);
     t.one_tw = to_tw(pr, 1);
+    for (int k = 0; k < 8; ++k) {
+      t.c16[k] = to_tw(pr, c16[k]);
+      t.c16i[k] = to_tw(pr, c16i[k]);
+    }
     memcpy(c->rt, &t, sizeof(t));
   } else {
     RootTable<uint32_t> t;
@@ -218,6 +228,10 @@ void build_root_table(tft_ctx* c) {
     }
     t.half_tw = (uint32_t)to_tw(pr, half);
     t.one_tw = (uint32_t)to_tw(pr, 1);
+    for (int k = 0; k < 8; ++k) {
+      t.c16[k] = (uint32_t)to_tw(pr, c16[k]);
+      t.c16i[k] = (uint32_t)to_tw(pr, c16i[k]);
+    }
     memcpy(c->rt, &t, sizeof(t));
   }
 }
@@ -290,6 +304,11 @@ tft_status from_cuda(tft_ctx* ctx, cudaError_t e) {
   note(e);
   if (ctx) ctx->sticky = TFT_ECUDA;
   return TFT_ECUDA;
+}
+
+// One staging slot: max_len words rounded up to 256 bytes.
+size_t stage_slot_bytes(const tft_ctx* ctx) {
+  return (ctx->max_len * ctx->pr.w + 255) & ~(size_t)255;
 }
 
 uint64_t omega_a_tw(tft_ctx* ctx, const Plan& P) {
@@ -370,7 +389,7 @@ tft_status tft_ctx_create(tft_prime prime, int device, uint64_t max_len,
     return TFT_ENOMEM;
   }
   if (flags & TFT_CTX_HOST_STAGING) {
-    if (cudaMalloc(&c->stage, 3 * max_len * w) != cudaSuccess) {
+    if (cudaMalloc(&c->stage, 3 * stage_slot_bytes(c)) != cudaSuccess) {
       cudaFree(c->work);
       cudaFree(c->scratch);
       free(c);
@@ -491,11 +510,12 @@ tft_status tft_polymul_host(tft_ctx* ctx, const void* a_host, uint64_t na,
   DeviceGuard g(ctx->device);
   if (!g.ok) return TFT_ECUDA;
   const size_t w = ctx->pr.w;
-  // staging layout: [out: max_len][a: max_len][b: max_len], each 16-B aligned
+  // staging layout: [out][a][b], each max_len words rounded up to 256 bytes
   unsigned char* base = (unsigned char*)ctx->stage;
+  const size_t slot = stage_slot_bytes(ctx);
   void* dout = base;
-  void* da = base + ctx->max_len * w;
-  void* db = base + 2 * ctx->max_len * w;
+  void* da = base + slot;
+  void* db = base + 2 * slot;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemcpyAsync(da, a_host, na * w, cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||

@@ -112,6 +112,8 @@ struct RootTable {
   T winv[33];    // omega_[j]^{-1}
   T half_tw;     // 1/2 in twiddle form
   T one_tw;      // 1 in twiddle form
+  T c16[8];      // omega_{2k}, k < 8: the twiddles of a 16-point network
+  T c16i[8];     // omega_{2k}^{-1} / 2
 };
 
 }  // namespace tftgb

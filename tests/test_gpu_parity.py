@@ -334,3 +334,9 @@ def test_host_buffer_entry_points():
         assert np.array_equal(y, NV.alg1_tft(pr, x))
         tft.tft_inverse_host(ctx, y)
         assert np.array_equal(y, x)
+    # an odd max_len must still give 16-byte aligned staging slots
+    with tft.Context(2, 0, max_len=70001, host_staging=True) as ctx:
+        a, b = rand(pr, 30001, 4), rand(pr, 40000, 5)
+        out = np.zeros(a.size + b.size - 1, dtype=np.uint64)
+        tft.tft_polymul_host(ctx, a, b, out)
+        assert np.array_equal(out, NV.tft_polymul(pr, a, b))
