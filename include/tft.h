@@ -128,6 +128,36 @@ tft_status tft_polymul(tft_ctx* ctx, const void* a, uint64_t na,
                        const void* b, uint64_t nb, void* out, void* stream);
 
 /*
+ * tft_forward_noalloc: the in-place forward TFT of tft_forward, for callers
+ * that must not allocate device memory and so cannot create a context --
+ * for example a serving loop whose device memory is fully reserved at
+ * start-up and that may not call cudaMalloc (which can synchronize the
+ * device and stall other streams) while requests are in flight, or code
+ * running inside an allocator callback that cannot re-enter the allocator.
+ * The paper has no counterpart to this entry point; it is a deployment aid.
+ *   x, n, k, stream  as in tft_forward (x a 16-byte aligned device pointer
+ *                    on the calling thread's current device).
+ * Scratch: instead of a context, the call uses one fixed array of 2^14
+ * eight-byte words (128 KiB) in the library's static device memory.  Every
+ * GPU on which the library is loaded holds that array until the process
+ * exits.  Its size covers every length the library accepts:
+ * n <= 2^25 for 2^64 - 2^32 + 1 and n <= min(2^K, 2^27) for the two 32-bit
+ * primes; longer n returns TFT_ERANGE (and n > 2^k or k > K returns
+ * TFT_EINVAL) without launching anything.
+ * Set-up: the first call on each device resolves the array's device address
+ * and configures the kernels for that device (no allocation); make that
+ * first call before capturing any stream on that device.
+ * Sharing: all calls on a device use the same array, which keeps whatever
+ * the previous call left; each call writes every scratch word it reads, so
+ * nothing needs clearing.  Calls whose work overlaps on the GPU (different
+ * streams, or different host threads without ordering) race on the array;
+ * order them on one stream.
+ * Never calls cudaMalloc, cudaFree or any allocating routine.
+ */
+tft_status tft_forward_noalloc(tft_prime prime, void* x, uint64_t n,
+                               uint32_t k, void* stream);
+
+/*
  * Host-buffer variants: the same operations on HOST buffers.  Each call
  * copies the inputs to the context's staging buffers (cudaMemcpyAsync on
  * `stream`), runs the transform or product there, copies the result back and

@@ -317,7 +317,93 @@ uint64_t omega_a_tw(tft_ctx* ctx, const Plan& P) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Scratch for tft_forward_noalloc: a fixed array in device memory instead of
+// a context.  Its capacity covers the scratch of every plan the library makes
+// (one row of at most 2^14 words), whatever n is.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoallocScratchWords = (size_t)1 << 14;  // 128 KiB
+static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoallocScratchWords];
+
+namespace {
+
+struct NoallocDevice {
+  bool ready;
+  void* scratch;  // device address of g_noalloc_scratch on this device
+  int nsm;
+};
+
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc[64];
+
+// Once per device, with that device current: resolve the array's device
+// address (the host-side name is only a stand-in), read the SM count and set
+// the kernels' shared-memory limits for `prime`.
+tft_status noalloc_setup(int prime, int dev, NoallocDevice** out) {
+  if (dev < 0 || dev >= 64) return TFT_EINVAL;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  NoallocDevice& d = g_noalloc[dev];
+  if (!d.ready) {
+    void* p = nullptr;
+    if (note(cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess)
+      return TFT_ECUDA;
+    int nsm = 0;
+    if (note(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount,
+                                    dev)) != cudaSuccess)
+      return TFT_ECUDA;
+    d.scratch = p;
+    d.nsm = nsm;
+    d.ready = true;
+  }
+  {
+    std::lock_guard<std::mutex> lk2(g_prep_mu);
+    if (!g_prepared[prime][dev]) {
+      int optin = 0;
+      if (note(cudaDeviceGetAttribute(&optin,
+                                      cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                      dev)) != cudaSuccess)
+        return TFT_ECUDA;
+      if (note(prepare_kernels(prime, (size_t)optin)) != cudaSuccess)
+        return TFT_ECUDA;
+      g_prepared[prime][dev] = true;
+    }
+  }
+  *out = &d;
+  return TFT_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+tft_status tft_forward_noalloc(tft_prime prime, void* x, uint64_t n,
+                               uint32_t k, void* stream) {
+  if (!valid_prime((int)prime) || !x || n == 0) return TFT_EINVAL;
+  const PrimeInfo& pr = kPrimes[(int)prime];
+  if ((int)k > pr.K || (k < 64 && n > (1ull << k))) return TFT_EINVAL;
+  if (!aligned16(x)) return TFT_EINVAL;
+  Plan P;
+  if (!make_plan((int)prime, n, &P)) return TFT_ERANGE;
+  const uint64_t need_words = P.small ? 0 : (1ull << P.lr);
+  if (need_words * pr.w > sizeof(g_noalloc_scratch)) return TFT_ERANGE;
+  int dev = -1;
+  if (note(cudaGetDevice(&dev)) != cudaSuccess) return TFT_ECUDA;
+  NoallocDevice* d = nullptr;
+  tft_status st = noalloc_setup((int)prime, dev, &d);
+  if (st != TFT_OK) return st;
+  // The root table is built on the stack; nothing is allocated.
+  tft_ctx tmp;
+  memset(&tmp, 0, sizeof(tmp));
+  tmp.pr = pr;
+  build_root_table(&tmp);
+  cudaError_t e = launch_forward((int)prime, x, n, P, d->scratch, tmp.rt,
+                                 d->nsm, (cudaStream_t)stream, nullptr);
+  if (e != cudaSuccess) {
+    note(e);
+    return TFT_ECUDA;
+  }
+  return TFT_OK;
+}
 
 tft_status tft_ctx_create(tft_prime prime, int device, uint64_t max_len,
                           uint32_t flags, tft_ctx** out) {

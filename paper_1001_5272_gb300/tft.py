@@ -70,6 +70,7 @@ def load():
                                    ctypes.POINTER(u64)]),
         "tft_kernel_name": (ctypes.c_char_p, [i32]),
         "tft_launch_count": (u64, [vp]),
+        "tft_forward_noalloc": (i32, [i32, vp, u64, u32, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -292,3 +293,21 @@ def tft_profile_read(ctx):
 
 def tft_launch_count(ctx):
     return int(load().tft_launch_count(ctx.handle))
+
+
+def tft_forward_noalloc(prime, x, k=None, stream=None):
+    """In-place forward TFT without a context and without allocating device
+    memory: for callers that may not call cudaMalloc (for example a serving
+    loop whose memory is fully reserved up front).  The library's fixed
+    128 KiB device array serves as scratch; calls that overlap on the GPU
+    race on it, so order them on one stream.  Make the first call on a
+    device before any stream capture (it configures the device)."""
+    pid = prime_id(prime)
+    n = x.numel()
+    k = _default_k(n) if k is None else int(k)
+    L = load()
+    _check(L.tft_forward_noalloc(pid, _dev_ptr(x, int(L.tft_element_bytes(pid)),
+                                               "x"),
+                                 n, k, _stream_handle(stream)),
+           "tft_forward_noalloc")
+    return x
