@@ -182,7 +182,27 @@ struct tft_ctx {
   double prof_ms[K_NUM_KINDS];
   uint64_t prof_count[K_NUM_KINDS];
   LaunchHook hook;
+  AuxStreams aux;    // side stream + fork/join events
 };
+
+namespace {
+
+// Release everything a (possibly partly built) context owns.
+void ctx_release(tft_ctx* c) {
+  for (int i = 0; i < kProfSlots; ++i) {
+    if (c->prof[i].start) cudaEventDestroy(c->prof[i].start);
+    if (c->prof[i].stop) cudaEventDestroy(c->prof[i].stop);
+  }
+  if (c->aux.fork) cudaEventDestroy(c->aux.fork);
+  if (c->aux.join) cudaEventDestroy(c->aux.join);
+  if (c->aux.side) cudaStreamDestroy(c->aux.side);
+  if (c->stage) cudaFree(c->stage);
+  if (c->work) cudaFree(c->work);
+  if (c->scratch) cudaFree(c->scratch);
+  free(c);
+}
+
+}  // namespace
 
 namespace {
 
@@ -397,7 +417,8 @@ tft_status tft_forward_noalloc(tft_prime prime, void* x, uint64_t n,
   tmp.pr = pr;
   build_root_table(&tmp);
   cudaError_t e = launch_forward((int)prime, x, n, P, d->scratch, tmp.rt,
-                                 d->nsm, (cudaStream_t)stream, nullptr);
+                                 d->nsm, (cudaStream_t)stream, nullptr,
+                                 nullptr);
   if (e != cudaSuccess) {
     note(e);
     return TFT_ECUDA;
@@ -452,33 +473,28 @@ tft_status tft_ctx_create(tft_prime prime, int device, uint64_t max_len,
   for (int i = 0; i < kProfSlots; ++i) {
     if (note(cudaEventCreate(&c->prof[i].start)) != cudaSuccess ||
         note(cudaEventCreate(&c->prof[i].stop)) != cudaSuccess) {
-      for (int j = 0; j <= i; ++j) {
-        if (c->prof[j].start) cudaEventDestroy(c->prof[j].start);
-        if (c->prof[j].stop) cudaEventDestroy(c->prof[j].stop);
-      }
-      free(c);
+      ctx_release(c);
       return TFT_ECUDA;
     }
   }
-  const size_t w = pr.w;
-  if (cudaMalloc(&c->scratch, 3 * (1ull << 14) * w) != cudaSuccess) {
-    for (int i = 0; i < kProfSlots; ++i) {
-      cudaEventDestroy(c->prof[i].start);
-      cudaEventDestroy(c->prof[i].stop);
-    }
-    free(c);
-    return TFT_ENOMEM;
+  if (note(cudaStreamCreateWithFlags(&c->aux.side, cudaStreamNonBlocking)) !=
+          cudaSuccess ||
+      note(cudaEventCreateWithFlags(&c->aux.fork, cudaEventDisableTiming)) !=
+          cudaSuccess ||
+      note(cudaEventCreateWithFlags(&c->aux.join, cudaEventDisableTiming)) !=
+          cudaSuccess) {
+    ctx_release(c);
+    return TFT_ECUDA;
   }
-  if (cudaMalloc(&c->work, max_len * w) != cudaSuccess) {
-    cudaFree(c->scratch);
-    free(c);
+  const size_t w = pr.w;
+  if (cudaMalloc(&c->scratch, 3 * (1ull << 14) * w) != cudaSuccess ||
+      cudaMalloc(&c->work, max_len * w) != cudaSuccess) {
+    ctx_release(c);
     return TFT_ENOMEM;
   }
   if (flags & TFT_CTX_HOST_STAGING) {
     if (cudaMalloc(&c->stage, 3 * stage_slot_bytes(c)) != cudaSuccess) {
-      cudaFree(c->work);
-      cudaFree(c->scratch);
-      free(c);
+      ctx_release(c);
       return TFT_ENOMEM;
     }
   }
@@ -489,14 +505,7 @@ tft_status tft_ctx_create(tft_prime prime, int device, uint64_t max_len,
 tft_status tft_ctx_destroy(tft_ctx* ctx) {
   if (!ctx) return TFT_EINVAL;
   DeviceGuard g(ctx->device);
-  for (int i = 0; i < kProfSlots; ++i) {
-    if (ctx->prof[i].start) cudaEventDestroy(ctx->prof[i].start);
-    if (ctx->prof[i].stop) cudaEventDestroy(ctx->prof[i].stop);
-  }
-  if (ctx->stage) cudaFree(ctx->stage);
-  if (ctx->work) cudaFree(ctx->work);
-  if (ctx->scratch) cudaFree(ctx->scratch);
-  free(ctx);
+  ctx_release(ctx);
   return TFT_OK;
 }
 
@@ -510,7 +519,8 @@ tft_status tft_forward(tft_ctx* ctx, void* x, uint64_t n, uint32_t k,
   if (!g.ok) return TFT_ECUDA;
   return from_cuda(ctx, launch_forward(ctx->prime, x, n, P, ctx->scratch,
                                        ctx->rt, ctx->nsm,
-                                       (cudaStream_t)stream, &ctx->hook));
+                                       (cudaStream_t)stream, &ctx->hook,
+                                       &ctx->aux));
 }
 
 tft_status tft_inverse(tft_ctx* ctx, void* X, uint64_t n, uint32_t k,
@@ -547,7 +557,8 @@ tft_status tft_polymul(tft_ctx* ctx, const void* a, uint64_t na,
                                        ctx->work, EA, EB,
                                        P.small ? 0 : omega_a_tw(ctx, P),
                                        ctx->rt, ctx->nsm,
-                                       (cudaStream_t)stream, &ctx->hook));
+                                       (cudaStream_t)stream, &ctx->hook,
+                                       &ctx->aux));
 }
 
 static tft_status host_transform(tft_ctx* ctx, void* xh, uint64_t n,

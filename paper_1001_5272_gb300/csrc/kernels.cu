@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "engine.cuh"
+#include "rows.cuh"
 #include "tft_internal.h"
 
 namespace tftgb {
@@ -171,7 +172,7 @@ k_col_fwd(const typename F::T* src, uint64_t n_src, typename F::T* dst,
 template <class F>
 __global__ void __launch_bounds__(512)
 k_row_fwd(typename F::T* X, const typename F::T* __restrict__ E, int lr,
-          uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
+          uint64_t a, uint64_t b, int only_last, RootTable<typename F::T> rt) {
   using T = typename F::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RootTable<T> s_rt;
@@ -181,9 +182,11 @@ k_row_fwd(typename F::T* X, const typename F::T* __restrict__ E, int lr,
   T* W = Z + R;
   T* L = W + R / 2;
   build_base_tables<F>(W, nullptr, lr, s_rt);
-  const uint64_t nrows = a + (b > 0 ? 1 : 0);
+  // only_last: just the ragged last row (the full rows run elsewhere)
+  const uint64_t nrows = only_last ? 1 : a + (b > 0 ? 1 : 0);
   for (uint64_t it = blockIdx.x; it < nrows; it += gridDim.x) {
-    const uint64_t rho = (b > 0) ? (it == 0 ? a : it - 1) : it;
+    const uint64_t rho =
+        only_last ? a : ((b > 0) ? (it == 0 ? a : it - 1) : it);
     const bool last = rho == a;
     T* row = X + rho * R;
     for (uint32_t q = threadIdx.x; q < R; q += blockDim.x)
@@ -326,7 +329,7 @@ __global__ void __launch_bounds__(512)
 k_row_mul(typename F::T* out, const typename F::T* __restrict__ work,
           const typename F::T* __restrict__ EA,
           const typename F::T* __restrict__ EB, int lr, uint64_t a, uint64_t b,
-          RootTable<typename F::T> rt) {
+          int only_last, RootTable<typename F::T> rt) {
   using T = typename F::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RootTable<T> s_rt;
@@ -337,9 +340,10 @@ k_row_mul(typename F::T* out, const typename F::T* __restrict__ work,
   T* Wih = W + R / 2;
   T* L = Wih + R / 2;
   build_base_tables<F>(W, Wih, lr, s_rt);
-  const uint64_t nrows = a + (b > 0 ? 1 : 0);
+  const uint64_t nrows = only_last ? 1 : a + (b > 0 ? 1 : 0);
   for (uint64_t it = blockIdx.x; it < nrows; it += gridDim.x) {
-    const uint64_t rho = (b > 0) ? (it == 0 ? a : it - 1) : it;
+    const uint64_t rho =
+        only_last ? a : ((b > 0) ? (it == 0 ? a : it - 1) : it);
     const bool last = rho == a;
     T* orow = out + rho * R;
     const T* wrow = work + rho * R;
@@ -411,6 +415,12 @@ static cudaError_t set_smem(const void* fn, size_t optin) {
     __VA_ARGS__;                                     \
     if (H) H->after(H->user, (kind), s);             \
   } while (0)
+#define TFT_LAUNCH_ON(kind, strm, ...)               \
+  do {                                               \
+    if (H) H->before(H->user, (kind), (strm));       \
+    __VA_ARGS__;                                     \
+    if (H) H->after(H->user, (kind), (strm));        \
+  } while (0)
 
 template <class F>
 struct Launch {
@@ -428,12 +438,106 @@ struct Launch {
     if ((e = set_smem<F>((const void*)k_row_inv<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_row_mul<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_lastrow_inv<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_fwd2<F, 256>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_fwd2<F, 512>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_fwd2<F, 1024>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_inv2<F, 256>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_inv2<F, 512>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_inv2<F, 1024>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_mul2<F, 256>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_mul2<F, 512>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_row_mul2<F, 1024>, mx))) return e;
     return cudaSuccess;
   }
 
+  // Full rows run on the register-blocked engine (rows.cuh) when lr >= 8:
+  // R/16 threads per row, at least 256 threads per CTA.
+  static bool use_v2(const Plan& P) { return P.lr >= 8; }
+  static int v2_threads(int lr) {
+    const int tpr = 1 << (lr - 4);
+    return tpr < 256 ? 256 : tpr;
+  }
+  template <class K>
+  static uint32_t v2_grid(K kernel, int threads, size_t smem, uint64_t a,
+                          int G, int nsm) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads,
+                                                      smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    const uint64_t units = (a + G - 1) / G;
+    const uint64_t cap = (uint64_t)nsm * per_sm;
+    return (uint32_t)(units < cap ? units : cap);
+  }
+
+#define TFT_V2_DISPATCH(threads, CALL)                   \
+  switch (threads) {                                     \
+    case 256: { constexpr int MT = 256; CALL; } break;   \
+    case 512: { constexpr int MT = 512; CALL; } break;   \
+    default: { constexpr int MT = 1024; CALL; } break;   \
+  }
+
+  static cudaError_t rows_fwd_v2(T* x, const Plan& P, const RT& rt, int nsm,
+                                 cudaStream_t s, const LaunchHook* H) {
+    const int th = v2_threads(P.lr);
+    const int G = th >> (P.lr - 4);
+    const size_t sm = row_smem_bytes<T>(P.lr, G, 1);
+    TFT_V2_DISPATCH(th, {
+      const uint32_t grid = v2_grid(k_row_fwd2<F, MT>, th, sm, P.a, G, nsm);
+      TFT_LAUNCH(K_ROW_FWD,
+                 k_row_fwd2<F, MT><<<grid, th, sm, s>>>(x, P.lr, P.a, rt));
+    });
+    return cudaGetLastError();
+  }
+  static cudaError_t rows_inv_v2(T* x, const Plan& P, const RT& rt, int nsm,
+                                 cudaStream_t s, const LaunchHook* H) {
+    const int th = v2_threads(P.lr);
+    const int G = th >> (P.lr - 4);
+    const size_t sm = row_smem_bytes<T>(P.lr, G, 1);
+    TFT_V2_DISPATCH(th, {
+      const uint32_t grid = v2_grid(k_row_inv2<F, MT>, th, sm, P.a, G, nsm);
+      TFT_LAUNCH(K_ROW_INV,
+                 k_row_inv2<F, MT><<<grid, th, sm, s>>>(x, P.lr, P.a, rt));
+    });
+    return cudaGetLastError();
+  }
+  static cudaError_t rows_mul_v2(T* out, const T* work, const Plan& P,
+                                 const RT& rt, int nsm, cudaStream_t s,
+                                 const LaunchHook* H) {
+    const int th = v2_threads(P.lr);
+    const int G = th >> (P.lr - 4);
+    const size_t sm = row_smem_bytes<T>(P.lr, G, 2);
+    TFT_V2_DISPATCH(th, {
+      const uint32_t grid = v2_grid(k_row_mul2<F, MT>, th, sm, P.a, G, nsm);
+      TFT_LAUNCH(K_ROW_MUL, k_row_mul2<F, MT><<<grid, th, sm, s>>>(
+                                out, work, P.lr, P.a, rt));
+    });
+    return cudaGetLastError();
+  }
+
+  // Run `launch(stream)` for the ragged last row on the side stream, forked
+  // after the work already queued on s; join() makes s wait for it.
+  struct SideRow {
+    const AuxStreams* aux;
+    cudaStream_t s;
+    cudaStream_t side() const { return aux ? aux->side : s; }
+    void fork() const {
+      if (aux) {
+        cudaEventRecord(aux->fork, s);
+        cudaStreamWaitEvent(aux->side, aux->fork, 0);
+      }
+    }
+    void join() const {
+      if (aux) {
+        cudaEventRecord(aux->join, aux->side);
+        cudaStreamWaitEvent(s, aux->join, 0);
+      }
+    }
+  };
+
   static cudaError_t forward(T* x, uint64_t n, const Plan& P, T* E,
                              const RT& rt, int nsm, cudaStream_t s,
-                             const LaunchHook* H) {
+                             const LaunchHook* H, const AuxStreams* aux) {
     if (P.small) {
       TFT_LAUNCH(K_SMALL, k_small<F, false><<<1, 512,
                                               smem_small<F>(P.l, false), s>>>(
@@ -446,13 +550,28 @@ struct Launch {
                k_col_fwd<F><<<(R + C - 1) / C, 512,
                               smem_col<F>(P.c, P.clog, false), s>>>(
                    x, n, x, E, P.lr, P.a, P.b, P.c, P.clog, 0, R, rt));
-    const uint64_t rows = P.a + (P.b ? 1 : 0);
-    const uint32_t grid = (uint32_t)(rows < (uint64_t)nsm * P.row_ctas_per_sm
-                                         ? rows
-                                         : (uint64_t)nsm * P.row_ctas_per_sm);
-    TFT_LAUNCH(K_ROW_FWD, k_row_fwd<F><<<grid, 512, smem_row<F>(P.lr, 0), s>>>(
-                              x, E, P.lr, P.a, P.b, rt));
-    return cudaGetLastError();
+    if (!use_v2(P)) {
+      const uint64_t rows = P.a + (P.b ? 1 : 0);
+      const uint32_t grid =
+          (uint32_t)(rows < (uint64_t)nsm * P.row_ctas_per_sm
+                         ? rows
+                         : (uint64_t)nsm * P.row_ctas_per_sm);
+      TFT_LAUNCH(K_ROW_FWD,
+                 k_row_fwd<F><<<grid, 512, smem_row<F>(P.lr, 0), s>>>(
+                     x, E, P.lr, P.a, P.b, 0, rt));
+      return cudaGetLastError();
+    }
+    const SideRow side{aux, s};
+    if (P.b > 0) {
+      side.fork();
+      cudaStream_t s2 = side.side();
+      TFT_LAUNCH_ON(K_ROW_FWD, s2,
+                    k_row_fwd<F><<<1, 512, smem_row<F>(P.lr, 0), s2>>>(
+                        x, E, P.lr, P.a, P.b, 1, rt));
+    }
+    cudaError_t e = rows_fwd_v2(x, P, rt, nsm, s, H);
+    if (P.b > 0) side.join();
+    return e != cudaSuccess ? e : cudaGetLastError();
   }
 
   static cudaError_t inverse_tail(T* x, const Plan& P, T* E, T omega_a_tw,
@@ -491,7 +610,10 @@ struct Launch {
                                              s>>>(x, (uint32_t)n, P.l, rt));
       return cudaGetLastError();
     }
-    if (P.a > 0) {
+    if (P.a > 0 && use_v2(P)) {
+      cudaError_t e = rows_inv_v2(x, P, rt, nsm, s, H);
+      if (e != cudaSuccess) return e;
+    } else if (P.a > 0) {
       const uint32_t grid = (uint32_t)(P.a < (uint64_t)nsm * P.row_ctas_per_sm
                                            ? P.a
                                            : (uint64_t)nsm * P.row_ctas_per_sm);
@@ -505,7 +627,8 @@ struct Launch {
   static cudaError_t polymul(const T* a, uint64_t na, const T* b, uint64_t nb,
                              T* out, const Plan& P, T* work, T* EA, T* EB,
                              T omega_a_tw, const RT& rt, int nsm,
-                             cudaStream_t s, const LaunchHook* H) {
+                             cudaStream_t s, const LaunchHook* H,
+                             const AuxStreams* aux) {
     if (P.small) {
       TFT_LAUNCH(K_SMALL_MUL,
                  k_small_mul<F><<<1, 512, smem_small_mul<F>(P.l), s>>>(
@@ -521,12 +644,28 @@ struct Launch {
     TFT_LAUNCH(K_COL_FWD, k_col_fwd<F><<<(R + C - 1) / C, 512, sc, s>>>(
                               b, nb, work, EB, P.lr, P.a, P.b, P.c, P.clog, 0,
                               R, rt));
-    const uint64_t rows = P.a + (P.b ? 1 : 0);
-    const uint32_t grid = (uint32_t)(rows < (uint64_t)nsm * P.row_ctas_per_sm
-                                         ? rows
-                                         : (uint64_t)nsm * P.row_ctas_per_sm);
-    TFT_LAUNCH(K_ROW_MUL, k_row_mul<F><<<grid, 512, smem_row<F>(P.lr, 2), s>>>(
-                              out, work, EA, EB, P.lr, P.a, P.b, rt));
+    if (!use_v2(P)) {
+      const uint64_t rows = P.a + (P.b ? 1 : 0);
+      const uint32_t grid =
+          (uint32_t)(rows < (uint64_t)nsm * P.row_ctas_per_sm
+                         ? rows
+                         : (uint64_t)nsm * P.row_ctas_per_sm);
+      TFT_LAUNCH(K_ROW_MUL,
+                 k_row_mul<F><<<grid, 512, smem_row<F>(P.lr, 2), s>>>(
+                     out, work, EA, EB, P.lr, P.a, P.b, 0, rt));
+    } else {
+      const SideRow side{aux, s};
+      if (P.b > 0) {
+        side.fork();
+        cudaStream_t s2 = side.side();
+        TFT_LAUNCH_ON(K_ROW_MUL, s2,
+                      k_row_mul<F><<<1, 512, smem_row<F>(P.lr, 2), s2>>>(
+                          out, work, EA, EB, P.lr, P.a, P.b, 1, rt));
+      }
+      cudaError_t e = rows_mul_v2(out, work, P, rt, nsm, s, H);
+      if (P.b > 0) side.join();
+      if (e != cudaSuccess) return e;
+    }
     return inverse_tail(out, P, EA, omega_a_tw, rt, s, H);
   }
 };
@@ -562,10 +701,11 @@ cudaError_t prepare_kernels(int prime, size_t optin_smem) {
 
 cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
                            void* E, const void* rt, int nsm, cudaStream_t s,
-                           const LaunchHook* hook) {
+                           const LaunchHook* hook, const AuxStreams* aux) {
   TFT_DISPATCH(prime, return Launch<F>::forward(
                           (typename F::T*)x, n, P, (typename F::T*)E,
-                          *(const RootTable<typename F::T>*)rt, nsm, s, hook));
+                          *(const RootTable<typename F::T>*)rt, nsm, s, hook,
+                          aux));
 }
 
 cudaError_t launch_inverse(int prime, void* x, uint64_t n, const Plan& P,
@@ -582,14 +722,15 @@ cudaError_t launch_polymul(int prime, const void* a, uint64_t na,
                            const void* b, uint64_t nb, void* out,
                            const Plan& P, void* work, void* EA, void* EB,
                            uint64_t omega_a_tw, const void* rt, int nsm,
-                           cudaStream_t s, const LaunchHook* hook) {
+                           cudaStream_t s, const LaunchHook* hook,
+                           const AuxStreams* aux) {
   TFT_DISPATCH(prime,
                return Launch<F>::polymul(
                    (const typename F::T*)a, na, (const typename F::T*)b, nb,
                    (typename F::T*)out, P, (typename F::T*)work,
                    (typename F::T*)EA, (typename F::T*)EB,
                    (typename F::T)omega_a_tw,
-                   *(const RootTable<typename F::T>*)rt, nsm, s, hook));
+                   *(const RootTable<typename F::T>*)rt, nsm, s, hook, aux));
 }
 
 PlanSmem plan_smem(int prime, const Plan& P) {

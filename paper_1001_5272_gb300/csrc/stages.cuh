@@ -1,0 +1,185 @@
+// Register-blocked stages of the network for full power-of-two blocks.
+//
+// A block of R = 2^lr positions (one row of the row/column split, i.e. block
+// rho of the global network) is processed in stages of L <= 4 levels.  In a
+// stage covering levels r_lo + L - 1 .. r_lo, a "unit" is the 2^L positions
+//     p(u, i) = ((u >> r_lo) << (r_lo + L)) | (i << r_lo) | (u mod 2^r_lo),
+// i < 2^L, held in the registers of one thread.  In the remainder view of the
+// network (level r reduces modulo x^{2^r} - omega_{2 (y >> (r+1))}, eq. (1)),
+// such a unit holds the coefficients of g(z), z = x^{2^r_lo}, that must be
+// evaluated at the 2^L points omega_{B 2^L + s'} = omega_{B 2^L} omega_{s'}
+// (disjoint bits), where B = y >> (r_lo + L) is the unit's block index.  So a
+// stage is: multiply element i by zeta^i with zeta = omega_{B 2^L} (the
+// "twist"), then run the constant 2^L-point network whose twiddles
+// omega_{2k}, k < 2^{L-1}, are the same for every unit.  B splits into the
+// row's part and a local part, zeta = omega_{rho 2^{lr - r_lo}} *
+// omega_{B_local 2^L}; the first factor is one value per stage and row, the
+// second comes from a small per-CTA table (at most ~R/15 entries).
+//
+// The inverse stage undoes this exactly: the inverse constant network
+// (levels in increasing order, butterfly (X, Y) -> ((X+Y)/2,
+// omega_{2k}^{-1} (X-Y)/2), Algorithm 2's butterfly) and then the untwist by
+// zeta^{-i}.
+//
+// Shared memory holds a block with an XOR swizzle, phys(p) = p ^ ((p >> 4)
+// & 15), so that every stage's access pattern (unit-strided or contiguous)
+// touches distinct banks per half-warp.
+#pragma once
+#include "field.cuh"
+
+namespace tftgb {
+
+__device__ __forceinline__ uint32_t swz(uint32_t p) {
+  return p ^ ((p >> 4) & 15u);
+}
+
+// Stage descriptor: levels [r_lo, r_lo + L).
+struct StageDesc {
+  int r_lo;
+  int L;
+  int tl_off;  // offset of this stage's local twist table (2^{lr-r_lo-L})
+};
+
+// Stages of a block of 2^lr positions, forward order (highest levels first):
+// the first stage takes lr mod 4 levels (or 4), then stages of 4 down to 0.
+struct StagePlan {
+  int n;
+  StageDesc s[5];
+  int tl_total;
+};
+
+__host__ __device__ inline StagePlan make_stage_plan(int lr) {
+  StagePlan sp;
+  sp.n = 0;
+  int r = lr;
+  int first = lr % 4 ? lr % 4 : 4;
+  int L = first;
+  int off = 0;
+  while (r > 0) {
+    if (L > r) L = r;
+    sp.s[sp.n].r_lo = r - L;
+    sp.s[sp.n].L = L;
+    sp.s[sp.n].tl_off = off;
+    off += 1 << (lr - (r - L) - L);  // entries: 2^{lr - r_lo - L}
+    ++sp.n;
+    r -= L;
+    L = 4;
+  }
+  sp.tl_total = off;
+  return sp;
+}
+
+// Per-CTA constants of the stage engine, in shared memory.
+template <class T>
+struct StageConsts {
+  T c[8];    // omega_{2k}, k < 8 (twiddle form)
+  T ci[8];   // omega_{2k}^{-1} / 2 (twiddle form)
+};
+
+// Build the local twist tables TL[m] = omega_{m 2^L} and TLi (inverses) for
+// every stage: product of omega_[b + L + 1] over the set bits b of m.
+template <class F>
+__device__ void build_stage_tables(typename F::T* TL, typename F::T* TLi,
+                                   const StagePlan& sp, int lr,
+                                   const RootTable<typename F::T>& rt) {
+  using T = typename F::T;
+  for (int si = 0; si < sp.n; ++si) {
+    const int L = sp.s[si].L;
+    const int cnt = 1 << (lr - sp.s[si].r_lo - L);
+    for (int m = threadIdx.x; m < cnt; m += blockDim.x) {
+      T v = rt.one_tw, vi = rt.one_tw;
+      int bits = m, b = 0;
+      while (bits) {
+        if (bits & 1) {
+          v = F::mul_tw(v, rt.w[b + L + 1]);
+          vi = F::mul_tw(vi, rt.winv[b + L + 1]);
+        }
+        bits >>= 1;
+        ++b;
+      }
+      TL[sp.s[si].tl_off + m] = v;
+      TLi[sp.s[si].tl_off + m] = vi;
+    }
+  }
+}
+
+// omega_{rho 2^e} and its inverse: product of omega_[b + e + 1] over the set
+// bits b of rho (omega_{2^j} = omega_[j+1]).
+template <class F>
+__device__ __forceinline__ typename F::T row_factor(
+    uint64_t rho, int e, const RootTable<typename F::T>& rt, bool inverse) {
+  typename F::T v = rt.one_tw;
+  int b = 0;
+  while (rho) {
+    if (rho & 1) v = F::mul_tw(v, inverse ? rt.winv[b + e + 1] : rt.w[b + e + 1]);
+    rho >>= 1;
+    ++b;
+  }
+  return v;
+}
+
+// Powers zeta^i, i < 2^L (pw[0] is not used: the twist skips element 0).
+template <class F, int L>
+__device__ __forceinline__ void powers(typename F::T (&pw)[1 << L],
+                                       typename F::T zeta) {
+  pw[1] = zeta;
+#pragma unroll
+  for (int i = 2; i < (1 << L); ++i)
+    pw[i] = (i & 1) ? F::mul_tw(pw[i - 1], zeta)
+                    : F::mul_tw(pw[i / 2], pw[i / 2]);
+}
+
+template <class F, int L>
+__device__ __forceinline__ void cnet_fwd(typename F::T (&x)[1 << L],
+                                         const StageConsts<typename F::T>& K) {
+  using T = typename F::T;
+#pragma unroll
+  for (int d = L - 1; d >= 0; --d) {
+#pragma unroll
+    for (int i = 0; i < (1 << L); ++i) {
+      if (i & (1 << d)) continue;
+      const int k = i >> (d + 1);
+      const T w = x[i + (1 << d)];
+      const T m = k == 0 ? w : F::mul_tw(w, K.c[k]);
+      const T u = x[i];
+      x[i] = F::add(u, m);
+      x[i + (1 << d)] = F::sub(u, m);
+    }
+  }
+}
+
+template <class F, int L>
+__device__ __forceinline__ void cnet_inv(typename F::T (&x)[1 << L],
+                                         const StageConsts<typename F::T>& K) {
+  using T = typename F::T;
+#pragma unroll
+  for (int d = 0; d < L; ++d) {
+#pragma unroll
+    for (int i = 0; i < (1 << L); ++i) {
+      if (i & (1 << d)) continue;
+      const int k = i >> (d + 1);
+      const T X = x[i], Y = x[i + (1 << d)];
+      x[i] = F::half(F::add(X, Y));
+      const T df = F::sub(X, Y);
+      x[i + (1 << d)] = k == 0 ? F::half(df) : F::mul_tw(df, K.ci[k]);
+    }
+  }
+}
+
+template <class F, int L>
+__device__ __forceinline__ void twist(typename F::T (&x)[1 << L],
+                                      typename F::T zeta) {
+  typename F::T pw[1 << L];
+  powers<F, L>(pw, zeta);
+#pragma unroll
+  for (int i = 1; i < (1 << L); ++i) x[i] = F::mul_tw(x[i], pw[i]);
+}
+
+// Unit geometry of a stage.
+__device__ __forceinline__ uint32_t unit_pos(uint32_t u, int r_lo, int L,
+                                             int i) {
+  return ((u >> r_lo) << (r_lo + L)) | ((uint32_t)i << r_lo) |
+         (u & ((1u << r_lo) - 1));
+}
+
+}  // namespace tftgb

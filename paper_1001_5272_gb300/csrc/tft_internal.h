@@ -51,9 +51,18 @@ struct PlanSmem {
 cudaError_t prepare_kernels(int prime, size_t optin_smem);
 PlanSmem plan_smem(int prime, const Plan& P);
 
+// A second stream and two events owned by a context: independent pieces of a
+// call (the ragged last row next to the full rows) run concurrently, forked
+// from and joined back into the caller's stream.  Null: run serially.
+struct AuxStreams {
+  cudaStream_t side;
+  cudaEvent_t fork;
+  cudaEvent_t join;
+};
+
 cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
                            void* E, const void* rt, int nsm, cudaStream_t s,
-                           const LaunchHook* hook);
+                           const LaunchHook* hook, const AuxStreams* aux);
 cudaError_t launch_inverse(int prime, void* x, uint64_t n, const Plan& P,
                            void* E, uint64_t omega_a_tw, const void* rt,
                            int nsm, cudaStream_t s, const LaunchHook* hook);
@@ -61,6 +70,7 @@ cudaError_t launch_polymul(int prime, const void* a, uint64_t na,
                            const void* b, uint64_t nb, void* out,
                            const Plan& P, void* work, void* EA, void* EB,
                            uint64_t omega_a_tw, const void* rt, int nsm,
-                           cudaStream_t s, const LaunchHook* hook);
+                           cudaStream_t s, const LaunchHook* hook,
+                           const AuxStreams* aux);
 
 }  // namespace tftgb
