@@ -217,10 +217,13 @@ const char* tft_last_cuda_error(void);
  * returns, per kernel kind 0 .. TFT_NUM_KERNEL_KINDS-1, the summed duration
  * in milliseconds and the number of timed launches since the last
  * tft_profile_enable (which resets the totals).  Kind names come from
- * tft_kernel_name.  Profiling must be off while a stream is being captured
+ * tft_kernel_name; a kind names a kernel family (a column pass, a row pass,
+ * the ragged last row, ...).  Launches on the context's side stream run
+ * concurrently with the main stream, so their durations can include time
+ * spent waiting for an SM.  Profiling must be off while a stream is being captured
  * into a CUDA graph.
  */
-#define TFT_NUM_KERNEL_KINDS 8
+#define TFT_NUM_KERNEL_KINDS 10
 tft_status tft_profile_enable(tft_ctx* ctx, int enable);
 tft_status tft_profile_read(tft_ctx* ctx, double* ms, uint64_t* launches);
 const char* tft_kernel_name(int kind);

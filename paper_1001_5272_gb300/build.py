@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libtft_gb300.so")
-SOURCES = ["kernels.cu", "api.cu"]
+SOURCES = ["kernels_gold.cu", "kernels_p2013.cu", "kernels_p998.cu",
+           "dispatch.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

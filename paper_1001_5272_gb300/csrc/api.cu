@@ -107,8 +107,9 @@ bool make_plan(int prime, uint64_t n, Plan* out) {
   P.a = n >> lr;
   P.b = n & ((1ull << lr) - 1);
   P.c = ceil_log2(col_rows(lr));
-  // columns per CTA: the most (<= 16, <= R) whose tile fits ~200 KB
-  const size_t budget = 200 * 1024;
+  // columns per CTA: the most (<= 16, <= R) whose tile fits ~100 KB, so that
+  // two column CTAs share an SM
+  const size_t budget = 100 * 1024;
   int clog = 0;
   while (clog < 4 && (1 << (clog + 1)) <= (1 << lr)) {
     Plan Q = P;
@@ -705,8 +706,9 @@ tft_status tft_profile_read(tft_ctx* ctx, double* ms, uint64_t* launches) {
 
 const char* tft_kernel_name(int kind) {
   static const char* names[K_NUM_KINDS] = {
-      "k_small", "k_small_mul", "k_col_fwd", "k_row_fwd",
-      "k_row_inv", "k_col_inv", "k_lastrow_inv", "k_row_mul"};
+      "k_small",   "k_small_mul",   "k_col_fwd",     "k_row_fwd",
+      "k_row_inv", "k_col_inv",     "k_lastrow_inv", "k_row_mul",
+      "k_lastrow_fwd", "k_lastrow_mul"};
   return (kind >= 0 && kind < K_NUM_KINDS) ? names[kind] : "unknown";
 }
 

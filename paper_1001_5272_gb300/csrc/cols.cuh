@@ -1,0 +1,432 @@
+// Column kernels on the register-blocked stage engine (stages.cuh).
+//
+// A column tile holds C = 2^clog adjacent columns of the R-wide matrix view,
+// each padded to 2^c rows, row-major in shared memory: element (t, c) at
+// Z[tswz(t) * C + c].  tswz permutes rows inside each 16-row group by
+// XOR-ing the low 4 - clog bits of t with t >> 4, so that a warp touching C
+// columns of several 16-row groups hits distinct banks.  Every column is its
+// own transform (twiddles independent of the column), so a stage's twist is
+// omega_{B 2^L} with B the unit's block index inside the column: the row
+// factor of the row kernels is 1 here.
+#pragma once
+#include "stages.cuh"
+
+namespace tftgb {
+
+__device__ __forceinline__ uint32_t tswz(uint32_t t, int clog) {
+  return clog >= 4 ? t : t ^ ((t >> 4) & ((1u << (4 - clog)) - 1));
+}
+
+// Shared layout of the column kernels:
+//   K (StageConsts) | TL[tl] | TLi[tl] | Z[2^c * C]
+template <class T>
+struct ColSmem {
+  StageConsts<T>* K;
+  T* TL;
+  T* TLi;
+  T* Z;
+  __device__ ColSmem(unsigned char* raw, int tl) {
+    K = reinterpret_cast<StageConsts<T>*>(raw);
+    T* p = reinterpret_cast<T*>(raw + sizeof(StageConsts<T>));
+    TL = p;
+    p += tl;
+    TLi = p;
+    p += tl;
+    uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
+    Z = reinterpret_cast<T*>(a);
+  }
+};
+
+// (the tile area holds at least 256 words: the inverse kernel reuses it for
+// its Horner reduction)
+template <class T>
+__host__ __device__ inline size_t col_smem_bytes(int c, int clog) {
+  const StagePlan sp = make_stage_plan(c);
+  size_t b = sizeof(StageConsts<T>) + sizeof(T) * 2 * sp.tl_total;
+  b = (b + 15) & ~(size_t)15;
+  const size_t tile = (size_t)1 << (c + clog);
+  return b + sizeof(T) * (tile < 256 ? 256 : tile);
+}
+
+// One forward stage over all units of a column tile.  FIRST: inputs from
+// global memory (positions >= n_src and rows >= rows are zero); LAST: outputs
+// to global memory (rows t < a to dst, row a to dst or E).
+template <class F, int L, bool FIRST, bool LAST>
+__device__ __forceinline__ void col_fwd_stage(
+    typename F::T* Z, const typename F::T* src, uint64_t n_src,
+    typename F::T* dst, typename F::T* E, uint64_t R, uint64_t a, uint64_t b,
+    uint32_t rows, int c, int clog, uint32_t q0, uint32_t q_end, int r_lo,
+    const typename F::T* TLs, const StageConsts<typename F::T>& K) {
+  using T = typename F::T;
+  constexpr int U = 1 << L;
+  const uint32_t C = 1u << clog;
+  // rows still needed once this stage is done: < ceil(rows / 2^r_lo) 2^r_lo
+  const uint32_t need = ((rows + (1u << r_lo) - 1) >> r_lo) << r_lo;
+  const uint32_t units = 1u << (c - L + clog);
+#pragma unroll 1
+  for (uint32_t u = threadIdx.x; u < units; u += blockDim.x) {
+    const uint32_t cc = u & (C - 1);
+    const uint32_t ut = u >> clog;
+    const uint32_t bstart = (ut >> r_lo) << (r_lo + L);
+    if (bstart >= need) continue;
+    const uint64_t q = (uint64_t)q0 + cc;
+    const bool colok = q < q_end;
+    T x[U];
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const uint32_t t = unit_pos(ut, r_lo, L, i);
+      if (FIRST) {
+        const uint64_t pos = q + (uint64_t)t * R;
+        x[i] = (colok && t < rows && pos < n_src) ? src[pos] : T(0);
+      } else {
+        x[i] = Z[(tswz(t, clog) << clog) + cc];
+      }
+    }
+    // the first stage's block index is 0: zeta = 1, no twist
+    if (!FIRST) twist<F, L>(x, TLs[ut >> r_lo]);
+    cnet_fwd<F, L>(x, K);
+#pragma unroll
+    for (int i = 0; i < U; ++i) {
+      const uint32_t t = unit_pos(ut, r_lo, L, i);
+      if (LAST) {
+        if (colok && t < rows) {
+          if (t < a)
+            dst[q + (uint64_t)t * R] = x[i];
+          else if (q < b)
+            dst[q + a * R] = x[i];
+          else
+            E[q] = x[i];
+        }
+      } else {
+        Z[(tswz(t, clog) << clog) + cc] = x[i];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Forward column pass.  Rows produced: `rows` = a (+1 if b > 0).  Inputs at
+// positions >= n_src are the operand's zero extension.  A unit whose whole
+// block lies at or beyond the rows the later stages need is skipped (the
+// pruned network of engine.cuh, at stage granularity).  The last stage
+// writes straight to global memory: rows t < a to dst, row a to dst for long
+// columns (q < b) and to E for short ones.
+// ---------------------------------------------------------------------------
+template <class F, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+k_col_fwd2(const typename F::T* src, uint64_t n_src, typename F::T* dst,
+           typename F::T* __restrict__ E, int lr, uint64_t a, uint64_t b,
+           int c, int clog, uint32_t q_begin, uint32_t q_end,
+           RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  {
+    const T* s = reinterpret_cast<const T*>(&rt);
+    T* d = reinterpret_cast<T*>(&s_rt);
+    for (int i = threadIdx.x; i < (int)(sizeof(rt) / sizeof(T)); i += blockDim.x)
+      d[i] = s[i];
+  }
+  __syncthreads();
+  const StagePlan sp = make_stage_plan(c);
+  ColSmem<T> S(smem_raw, sp.tl_total);
+  for (int i = threadIdx.x; i < 8; i += blockDim.x) {
+    S.K->c[i] = s_rt.c16[i];
+    S.K->ci[i] = s_rt.c16i[i];
+  }
+  build_stage_tables<F>(S.TL, S.TLi, sp, c, s_rt);
+  __syncthreads();
+  const uint64_t R = 1ull << lr;
+  const uint32_t q0 = q_begin + blockIdx.x * (1u << clog);
+  const uint32_t rows = (uint32_t)(a + (b > 0 ? 1 : 0));
+  for (int si = 0; si < sp.n; ++si) {
+    const int r_lo = sp.s[si].r_lo;
+    const T* TLs = S.TL + sp.s[si].tl_off;
+    const bool first = si == 0, last = si == sp.n - 1;
+#define TFT_COL_FWD_CALL(FI, LA)                                            \
+  TFT_STAGE_SWITCH(sp.s[si].L,                                              \
+                   (col_fwd_stage<F, LL, FI, LA>(S.Z, src, n_src, dst, E, R, \
+                                                 a, b, rows, c, clog, q0,   \
+                                                 q_end, r_lo, TLs, *S.K)))
+    if (first && last) {
+      TFT_COL_FWD_CALL(true, true);
+    } else if (first) {
+      TFT_COL_FWD_CALL(true, false);
+    } else if (last) {
+      TFT_COL_FWD_CALL(false, true);
+    } else {
+      TFT_COL_FWD_CALL(false, false);
+    }
+#undef TFT_COL_FWD_CALL
+    __syncthreads();
+  }
+}
+
+// omega_{2j} (twiddle form) as the product of omega_[b+2] over the set bits b
+// of j (omega_{2^{b+1}} = omega_[b+2]); inverse: the inverse roots times 1/2.
+template <class F>
+__device__ __forceinline__ typename F::T col_theta(
+    uint32_t j, const RootTable<typename F::T>& rt, bool inv_half) {
+  typename F::T v = inv_half ? rt.half_tw : rt.one_tw;
+  int b = 0;
+  while (j) {
+    if (j & 1) v = F::mul_tw(v, inv_half ? rt.winv[b + 2] : rt.w[b + 2]);
+    j >>= 1;
+    ++b;
+  }
+  return v;
+}
+
+// One unit of an inverse stage (levels r_lo .. r_lo + L - 1) of the full
+// inverse network of the dyadic block [off, off + 2^k) of the tile: unit u
+// of the block covers column u mod C.  The block is block off >> k of the
+// column's network, so the stage twist is omega_{(off >> k) 2^{k - r_lo}} *
+// omega_{B_local 2^L} (inverted here, RFi is the first factor's inverse).
+template <class F, int L>
+__device__ __forceinline__ void col_inv_unit(
+    typename F::T* Z, int clog, uint32_t off, int r_lo, uint32_t u,
+    typename F::T RFi, const typename F::T* TL16i,
+    const StageConsts<typename F::T>& K) {
+  using T = typename F::T;
+  constexpr int U = 1 << L;
+  const uint32_t cc = u & ((1u << clog) - 1);
+  const uint32_t ut = u >> clog;
+  T x[U];
+#pragma unroll
+  for (int i = 0; i < U; ++i) {
+    const uint32_t t = off + unit_pos(ut, r_lo, L, i);
+    x[i] = Z[(tswz(t, clog) << clog) + cc];
+  }
+  cnet_inv<F, L>(x, K);
+  // only the 4-level stages below a block's top have B_local != 0
+  const uint32_t bl = ut >> r_lo;
+  twist<F, L>(x, L == 4 && bl ? F::mul_tw(RFi, TL16i[bl]) : RFi);
+#pragma unroll
+  for (int i = 0; i < U; ++i) {
+    const uint32_t t = off + unit_pos(ut, r_lo, L, i);
+    Z[(tswz(t, clog) << clog) + cc] = x[i];
+  }
+}
+
+// All units of width L of stage j across the dyadic blocks whose stage j has
+// that width, flattened over the CTA's threads.
+template <class F, int L>
+__device__ __forceinline__ void col_inv_stage_flat(
+    typename F::T* Z, int clog, int r_lo, int j, int nb, const int* bk,
+    const uint32_t* boff, const typename F::T* rfi,
+    const typename F::T* TL16i, const StageConsts<typename F::T>& K) {
+  uint32_t total = 0;
+  for (int i = 0; i < nb; ++i) {
+    const int w = bk[i] - r_lo;
+    if (w > 0 && (w >= 4 ? 4 : w) == L) total += 1u << (bk[i] - L + clog);
+  }
+#pragma unroll 1
+  for (uint32_t ug = threadIdx.x; ug < total; ug += blockDim.x) {
+    uint32_t u = ug;
+    int i = 0;
+    for (; i < nb; ++i) {
+      const int w = bk[i] - r_lo;
+      if (w <= 0 || (w >= 4 ? 4 : w) != L) continue;
+      const uint32_t cnt = 1u << (bk[i] - L + clog);
+      if (u < cnt) break;
+      u -= cnt;
+    }
+    col_inv_unit<F, L>(Z, clog, boff[i], r_lo, u, rfi[j * 14 + i], TL16i, K);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Inverse column pass over columns [q_begin, q_end), all of length m (a for
+// short columns, a + 1 for long ones), padded to 2^c in shared memory: the
+// generalized block inverse of engine.cuh (phase A: the full inverses of the
+// dyadic blocks of m; then one descent and one ascent), with phase A on the
+// stage engine.  With want_E also E_q = C_q(omega_a) by a parallel Horner
+// rule (omega_a in twiddle form).
+// ---------------------------------------------------------------------------
+template <class F, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+k_col_inv2(typename F::T* X, typename F::T* __restrict__ E, int lr,
+           uint32_t m, int c, int clog, uint32_t q_begin, uint32_t q_end,
+           int want_E, typename F::T omega_a_tw,
+           RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  {
+    const T* s = reinterpret_cast<const T*>(&rt);
+    T* d = reinterpret_cast<T*>(&s_rt);
+    for (int i = threadIdx.x; i < (int)(sizeof(rt) / sizeof(T)); i += blockDim.x)
+      d[i] = s[i];
+  }
+  __syncthreads();
+  // stage tables for 4-level stages: TL16[m'] = omega_{16 m'}, m' < 2^{c-4}
+  const StagePlan sp = make_stage_plan(c);
+  ColSmem<T> S(smem_raw, sp.tl_total);
+  for (int i = threadIdx.x; i < 8; i += blockDim.x) {
+    S.K->c[i] = s_rt.c16[i];
+    S.K->ci[i] = s_rt.c16i[i];
+  }
+  const uint32_t n16 = c > 4 ? 1u << (c - 4) : 1u;
+  T* TL16i = S.TLi;  // n16 <= tl_total entries (the last stage's table)
+  for (uint32_t j = threadIdx.x; j < n16; j += blockDim.x) {
+    T v = s_rt.one_tw;
+    uint32_t bits = j;
+    int b = 0;
+    while (bits) {
+      if (bits & 1) v = F::mul_tw(v, s_rt.winv[b + 5]);  // omega_{16 2^b}
+      bits >>= 1;
+      ++b;
+    }
+    TL16i[j] = v;
+  }
+  const uint32_t C = 1u << clog;
+  const uint64_t R = 1ull << lr;
+  const uint32_t q0 = q_begin + blockIdx.x * C;
+  const uint32_t N = 1u << c;
+  T* Z = S.Z;
+  for (uint32_t i = threadIdx.x; i < (N << clog); i += blockDim.x) {
+    const uint32_t t = i >> clog, cc = i & (C - 1);
+    const uint64_t q = (uint64_t)q0 + cc;
+    Z[(tswz(t, clog) << clog) + cc] =
+        (q < q_end && t < m) ? X[q + (uint64_t)t * R] : T(0);
+  }
+  __syncthreads();
+  // ---- phase A: full inverse of every dyadic block of m ------------------
+  // The blocks are the set bits k of m (sizes 2^k, decreasing, at increasing
+  // offsets); m = 2^c is the single block of the whole column.  Stage j
+  // covers levels 4j .. 4j + 3 (fewer at a block's top); blocks are
+  // independent, so the units of all blocks are processed together and one
+  // barrier separates stage indices.
+  __shared__ int s_bk[14];
+  __shared__ uint32_t s_boff[14];
+  __shared__ T s_rfi[4 * 14];
+  __shared__ int s_nb;
+  if (threadIdx.x == 0) {
+    int nb = 0;
+    uint32_t off = 0;
+    for (int k = c; k >= 1; --k) {
+      const bool block = (k == c) ? (m == N) : (((m >> k) & 1u) != 0);
+      if (!block) continue;
+      s_bk[nb] = k;
+      s_boff[nb] = off;
+      ++nb;
+      off += 1u << k;
+    }
+    s_nb = nb;
+  }
+  __syncthreads();
+  const int nb = s_nb;
+  const int nst = (c + 3) / 4;
+  for (int e = threadIdx.x; e < nst * nb; e += blockDim.x) {
+    const int jj = e / nb, i = e % nb;
+    const int k = s_bk[i];
+    s_rfi[jj * 14 + i] = k > 4 * jj ? row_factor<F>(s_boff[i] >> k,
+                                                    k - 4 * jj, s_rt, true)
+                                    : s_rt.one_tw;
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nst; ++jj) {
+    const int r_lo = 4 * jj;
+    col_inv_stage_flat<F, 4>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
+                             TL16i, *S.K);
+    col_inv_stage_flat<F, 3>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
+                             TL16i, *S.K);
+    col_inv_stage_flat<F, 2>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
+                             TL16i, *S.K);
+    col_inv_stage_flat<F, 1>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
+                             TL16i, *S.K);
+    __syncthreads();
+  }
+  // ---- descent and ascent (one level each) -------------------------------
+  if (m != N) {
+    int lstop = 0;
+    for (int l = c; l >= 1; --l) {
+      const uint32_t low = m & ((1u << l) - 1);
+      if (low == 0) {
+        lstop = l;
+        break;
+      }
+      const uint32_t B = m & ~((1u << l) - 1);
+      const uint32_t h = 1u << (l - 1);
+      const T th = col_theta<F>(B >> l, s_rt, false);
+      const uint32_t j0 = low >= h ? low - h : low;
+      const uint32_t cnt = (h - j0) << clog;
+      for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint32_t cc = i & (C - 1);
+        const uint32_t jj = j0 + (i >> clog);
+        T* pl = Z + (tswz(B + jj, clog) << clog) + cc;
+        T* pu = Z + (tswz(B + h + jj, clog) << clog) + cc;
+        if (low >= h) {
+          const T tt = F::mul_tw(*pu, th);
+          *pu = F::sub(F::sub(*pl, tt), tt);
+        } else {
+          *pl = F::add(*pl, F::mul_tw(*pu, th));
+        }
+      }
+      __syncthreads();
+    }
+    for (int l = lstop + 1; l <= c; ++l) {
+      const uint32_t low = m & ((1u << l) - 1);
+      const uint32_t B = m & ~((1u << l) - 1);
+      const uint32_t h = 1u << (l - 1);
+      const uint32_t cnt = h << clog;
+      const bool up = low >= h;
+      const T th = col_theta<F>(B >> l, s_rt, up);
+      for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const uint32_t cc = i & (C - 1);
+        const uint32_t jj = i >> clog;
+        T* pl = Z + (tswz(B + jj, clog) << clog) + cc;
+        T* pu = Z + (tswz(B + h + jj, clog) << clog) + cc;
+        if (up) {
+          const T Xv = *pl, Yv = *pu;
+          *pl = F::half(F::add(Xv, Yv));
+          *pu = F::mul_tw(F::sub(Xv, Yv), th);
+        } else {
+          *pl = F::sub(*pl, F::mul_tw(*pu, th));
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---- store and E ---------------------------------------------------------
+  for (uint32_t i = threadIdx.x; i < (m << clog); i += blockDim.x) {
+    const uint32_t t = i >> clog, cc = i & (C - 1);
+    const uint64_t q = (uint64_t)q0 + cc;
+    if (q < q_end) X[q + (uint64_t)t * R] = Z[(tswz(t, clog) << clog) + cc];
+  }
+  if (want_E) {
+    const uint32_t tpc = blockDim.x >> clog;  // threads per column
+    const uint32_t cc = threadIdx.x & (C - 1);
+    const uint32_t kk = threadIdx.x >> clog;
+    const uint32_t chunk = (m + tpc - 1) / tpc;
+    const uint32_t t0 = kk * chunk;
+    const uint32_t t1 = t0 + chunk < m ? t0 + chunk : m;
+    T acc = 0;
+    for (uint32_t t = t1; t > t0; --t)
+      acc = F::add(F::mul_tw(acc, omega_a_tw),
+                   Z[(tswz(t - 1, clog) << clog) + cc]);
+    if (t0 < m) {
+      T pw = s_rt.one_tw, base = omega_a_tw;
+      for (uint32_t e = t0; e; e >>= 1) {
+        if (e & 1) pw = F::mul_tw(pw, base);
+        base = F::mul_tw(base, base);
+      }
+      acc = F::mul_tw(acc, pw);
+    } else {
+      acc = 0;
+    }
+    __syncthreads();
+    T* part = Z;  // the tile is no longer needed
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < C) {
+      T sacc = 0;
+      for (uint32_t k2 = 0; k2 < tpc; ++k2)
+        sacc = F::add(sacc, part[(k2 << clog) + threadIdx.x]);
+      const uint64_t q = (uint64_t)q0 + threadIdx.x;
+      if (q < q_end) E[q] = sacc;
+    }
+  }
+}
+
+}  // namespace tftgb

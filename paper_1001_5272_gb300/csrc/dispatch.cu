@@ -1,0 +1,78 @@
+// Prime dispatch: forwards each launcher to the field's translation unit.
+#include "tft_internal.h"
+
+namespace tftgb {
+
+#define TFT_FIELD_DECLS(NAME)                                                 \
+  cudaError_t NAME##_prepare(size_t optin);                                   \
+  cudaError_t NAME##_forward(void* x, uint64_t n, const Plan& P, void* E,     \
+                             const void* rt, int nsm, cudaStream_t s,         \
+                             const LaunchHook* hook, const AuxStreams* aux);  \
+  cudaError_t NAME##_inverse(void* x, uint64_t n, const Plan& P, void* E,     \
+                             uint64_t omega_a_tw, const void* rt, int nsm,    \
+                             cudaStream_t s, const LaunchHook* hook);         \
+  cudaError_t NAME##_polymul(const void* a, uint64_t na, const void* b,       \
+                             uint64_t nb, void* out, const Plan& P,           \
+                             void* work, void* EA, void* EB,                  \
+                             uint64_t omega_a_tw, const void* rt, int nsm,    \
+                             cudaStream_t s, const LaunchHook* hook,          \
+                             const AuxStreams* aux);                          \
+  PlanSmem NAME##_plan_smem(const Plan& P);
+
+TFT_FIELD_DECLS(p998)
+TFT_FIELD_DECLS(p2013)
+TFT_FIELD_DECLS(gold)
+
+#define TFT_BY_PRIME(prime, CALL0, CALL1, CALL2) \
+  switch (prime) {                               \
+    case 0: return CALL0;                        \
+    case 1: return CALL1;                        \
+    case 2: return CALL2;                        \
+    default: return cudaErrorInvalidValue;       \
+  }
+
+cudaError_t prepare_kernels(int prime, size_t optin) {
+  TFT_BY_PRIME(prime, p998_prepare(optin), p2013_prepare(optin),
+               gold_prepare(optin));
+}
+
+cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
+                           void* E, const void* rt, int nsm, cudaStream_t s,
+                           const LaunchHook* hook, const AuxStreams* aux) {
+  TFT_BY_PRIME(prime, p998_forward(x, n, P, E, rt, nsm, s, hook, aux),
+               p2013_forward(x, n, P, E, rt, nsm, s, hook, aux),
+               gold_forward(x, n, P, E, rt, nsm, s, hook, aux));
+}
+
+cudaError_t launch_inverse(int prime, void* x, uint64_t n, const Plan& P,
+                           void* E, uint64_t omega_a_tw, const void* rt,
+                           int nsm, cudaStream_t s, const LaunchHook* hook) {
+  TFT_BY_PRIME(prime, p998_inverse(x, n, P, E, omega_a_tw, rt, nsm, s, hook),
+               p2013_inverse(x, n, P, E, omega_a_tw, rt, nsm, s, hook),
+               gold_inverse(x, n, P, E, omega_a_tw, rt, nsm, s, hook));
+}
+
+cudaError_t launch_polymul(int prime, const void* a, uint64_t na,
+                           const void* b, uint64_t nb, void* out,
+                           const Plan& P, void* work, void* EA, void* EB,
+                           uint64_t omega_a_tw, const void* rt, int nsm,
+                           cudaStream_t s, const LaunchHook* hook,
+                           const AuxStreams* aux) {
+  TFT_BY_PRIME(prime,
+               p998_polymul(a, na, b, nb, out, P, work, EA, EB, omega_a_tw,
+                            rt, nsm, s, hook, aux),
+               p2013_polymul(a, na, b, nb, out, P, work, EA, EB, omega_a_tw,
+                             rt, nsm, s, hook, aux),
+               gold_polymul(a, na, b, nb, out, P, work, EA, EB, omega_a_tw,
+                            rt, nsm, s, hook, aux));
+}
+
+PlanSmem plan_smem(int prime, const Plan& P) {
+  switch (prime) {
+    case 0: return p998_plan_smem(P);
+    case 1: return p2013_plan_smem(P);
+    default: return gold_plan_smem(P);
+  }
+}
+
+}  // namespace tftgb

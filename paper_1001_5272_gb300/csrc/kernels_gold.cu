@@ -1,0 +1,6 @@
+// Kernels and launchers instantiated for one field (Goldilocks).
+#include "kernels_impl.cuh"
+
+namespace tftgb {
+TFT_DEFINE_FIELD_ENTRIES(Goldilocks, gold)
+}  // namespace tftgb

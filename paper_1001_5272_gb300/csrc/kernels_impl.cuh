@@ -21,9 +21,11 @@
 // generalized block inverse with known inputs E_q at q >= b; inverse long
 // columns (length a + 1).  Global memory holds the n-word buffer plus the
 // R-word scratch; every transform works in shared memory.
+#pragma once
 #include <cuda_runtime.h>
 
 #include "engine.cuh"
+#include "cols.cuh"
 #include "rows.cuh"
 #include "tft_internal.h"
 
@@ -427,8 +429,17 @@ struct Launch {
   using T = typename F::T;
   using RT = RootTable<T>;
 
+#define TFT_PREP_LR(LRV)                                                   \
+  do {                                                                     \
+    if ((e = set_smem<F>((const void*)k_row_fwd2<F, LRV>, mx))) return e;  \
+    if ((e = set_smem<F>((const void*)k_row_inv2<F, LRV>, mx))) return e;  \
+    if ((e = set_smem<F>((const void*)k_row_mul2<F, LRV>, mx))) return e;  \
+  } while (0)
+
   static cudaError_t prepare(size_t mx) {
     cudaError_t e;
+    if ((e = set_smem<F>((const void*)k_col_fwd2<F, 256>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_col_inv2<F, 256>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_small<F, false>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_small<F, true>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_small_mul<F>, mx))) return e;
@@ -438,25 +449,19 @@ struct Launch {
     if ((e = set_smem<F>((const void*)k_row_inv<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_row_mul<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_lastrow_inv<F>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_row_fwd2<F, 256>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_row_fwd2<F, 512>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_row_fwd2<F, 1024>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_row_inv2<F, 256>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_row_inv2<F, 512>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_row_inv2<F, 1024>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_row_mul2<F, 256>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_row_mul2<F, 512>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_row_mul2<F, 1024>, mx))) return e;
+    TFT_PREP_LR(8);
+    TFT_PREP_LR(9);
+    TFT_PREP_LR(10);
+    TFT_PREP_LR(11);
+    TFT_PREP_LR(12);
+    TFT_PREP_LR(13);
+    TFT_PREP_LR(14);
     return cudaSuccess;
   }
 
   // Full rows run on the register-blocked engine (rows.cuh) when lr >= 8:
   // R/16 threads per row, at least 256 threads per CTA.
   static bool use_v2(const Plan& P) { return P.lr >= 8; }
-  static int v2_threads(int lr) {
-    const int tpr = 1 << (lr - 4);
-    return tpr < 256 ? 256 : tpr;
-  }
   template <class K>
   static uint32_t v2_grid(K kernel, int threads, size_t smem, uint64_t a,
                           int G, int nsm) {
@@ -470,48 +475,57 @@ struct Launch {
     return (uint32_t)(units < cap ? units : cap);
   }
 
-#define TFT_V2_DISPATCH(threads, CALL)                   \
-  switch (threads) {                                     \
-    case 256: { constexpr int MT = 256; CALL; } break;   \
-    case 512: { constexpr int MT = 512; CALL; } break;   \
-    default: { constexpr int MT = 1024; CALL; } break;   \
-  }
-
   static cudaError_t rows_fwd_v2(T* x, const Plan& P, const RT& rt, int nsm,
                                  cudaStream_t s, const LaunchHook* H) {
-    const int th = v2_threads(P.lr);
-    const int G = th >> (P.lr - 4);
-    const size_t sm = row_smem_bytes<T>(P.lr, G, 1);
-    TFT_V2_DISPATCH(th, {
-      const uint32_t grid = v2_grid(k_row_fwd2<F, MT>, th, sm, P.a, G, nsm);
-      TFT_LAUNCH(K_ROW_FWD,
-                 k_row_fwd2<F, MT><<<grid, th, sm, s>>>(x, P.lr, P.a, rt));
+    TFT_LR_DISPATCH(P.lr, {
+      using Geo = RowGeom<LR>;
+      const size_t sm = row_smem_bytes<T>(LR, Geo::G, 1);
+      const uint32_t grid =
+          v2_grid(k_row_fwd2<F, LR>, Geo::THREADS, sm, P.a, Geo::G, nsm);
+      TFT_LAUNCH(K_ROW_FWD, k_row_fwd2<F, LR><<<grid, Geo::THREADS, sm, s>>>(
+                                x, P.a, rt));
     });
     return cudaGetLastError();
   }
   static cudaError_t rows_inv_v2(T* x, const Plan& P, const RT& rt, int nsm,
                                  cudaStream_t s, const LaunchHook* H) {
-    const int th = v2_threads(P.lr);
-    const int G = th >> (P.lr - 4);
-    const size_t sm = row_smem_bytes<T>(P.lr, G, 1);
-    TFT_V2_DISPATCH(th, {
-      const uint32_t grid = v2_grid(k_row_inv2<F, MT>, th, sm, P.a, G, nsm);
-      TFT_LAUNCH(K_ROW_INV,
-                 k_row_inv2<F, MT><<<grid, th, sm, s>>>(x, P.lr, P.a, rt));
+    TFT_LR_DISPATCH(P.lr, {
+      using Geo = RowGeom<LR>;
+      const size_t sm = row_smem_bytes<T>(LR, Geo::G, 1);
+      const uint32_t grid =
+          v2_grid(k_row_inv2<F, LR>, Geo::THREADS, sm, P.a, Geo::G, nsm);
+      TFT_LAUNCH(K_ROW_INV, k_row_inv2<F, LR><<<grid, Geo::THREADS, sm, s>>>(
+                                x, P.a, rt));
     });
     return cudaGetLastError();
   }
   static cudaError_t rows_mul_v2(T* out, const T* work, const Plan& P,
                                  const RT& rt, int nsm, cudaStream_t s,
                                  const LaunchHook* H) {
-    const int th = v2_threads(P.lr);
-    const int G = th >> (P.lr - 4);
-    const size_t sm = row_smem_bytes<T>(P.lr, G, 2);
-    TFT_V2_DISPATCH(th, {
-      const uint32_t grid = v2_grid(k_row_mul2<F, MT>, th, sm, P.a, G, nsm);
-      TFT_LAUNCH(K_ROW_MUL, k_row_mul2<F, MT><<<grid, th, sm, s>>>(
-                                out, work, P.lr, P.a, rt));
+    TFT_LR_DISPATCH(P.lr, {
+      using Geo = RowGeom<LR>;
+      const size_t sm = row_smem_bytes<T>(LR, Geo::G, 2);
+      const uint32_t grid =
+          v2_grid(k_row_mul2<F, LR>, Geo::THREADS, sm, P.a, Geo::G, nsm);
+      TFT_LAUNCH(K_ROW_MUL, k_row_mul2<F, LR><<<grid, Geo::THREADS, sm, s>>>(
+                                out, work, P.a, rt));
     });
+    return cudaGetLastError();
+  }
+
+  // Forward column pass on the stage engine: C = 2^clog columns per CTA,
+  // 16 elements per thread and stage, at most 256 threads.
+  static cudaError_t cols_fwd_v2(const T* src, uint64_t n_src, T* dst, T* E,
+                                 const Plan& P, const RT& rt, cudaStream_t s,
+                                 const LaunchHook* H) {
+    const uint32_t R = 1u << P.lr;
+    const uint32_t C = 1u << P.clog;
+    const uint64_t units = (uint64_t)C << (P.c > 4 ? P.c - 4 : 0);
+    const int th = units >= 256 ? 256 : (units < 32 ? 32 : (int)units);
+    const size_t sm = col_smem_bytes<T>(P.c, P.clog);
+    TFT_LAUNCH(K_COL_FWD, k_col_fwd2<F, 256><<<(R + C - 1) / C, th, sm, s>>>(
+                              src, n_src, dst, E, P.lr, P.a, P.b, P.c, P.clog,
+                              0, R, rt));
     return cudaGetLastError();
   }
 
@@ -544,12 +558,7 @@ struct Launch {
                               x, (uint32_t)n, P.l, rt));
       return cudaGetLastError();
     }
-    const uint32_t R = 1u << P.lr;
-    const uint32_t C = 1u << P.clog;
-    TFT_LAUNCH(K_COL_FWD,
-               k_col_fwd<F><<<(R + C - 1) / C, 512,
-                              smem_col<F>(P.c, P.clog, false), s>>>(
-                   x, n, x, E, P.lr, P.a, P.b, P.c, P.clog, 0, R, rt));
+    cols_fwd_v2(x, n, x, E, P, rt, s, H);
     if (!use_v2(P)) {
       const uint64_t rows = P.a + (P.b ? 1 : 0);
       const uint32_t grid =
@@ -565,7 +574,7 @@ struct Launch {
     if (P.b > 0) {
       side.fork();
       cudaStream_t s2 = side.side();
-      TFT_LAUNCH_ON(K_ROW_FWD, s2,
+      TFT_LAUNCH_ON(K_LASTROW_FWD, s2,
                     k_row_fwd<F><<<1, 512, smem_row<F>(P.lr, 0), s2>>>(
                         x, E, P.lr, P.a, P.b, 1, rt));
     }
@@ -579,12 +588,12 @@ struct Launch {
                                   const LaunchHook* H) {
     const uint32_t R = 1u << P.lr;
     const uint32_t C = 1u << P.clog;
+    const size_t sm = col_smem_bytes<T>(P.c, P.clog);
     // short columns q in [b, R): length a, and E_q = C_q(omega_a)
     if (P.a > 0 && P.b < R) {
       const uint32_t qb = (uint32_t)P.b;
       TFT_LAUNCH(K_COL_INV,
-                 k_col_inv<F><<<(R - qb + C - 1) / C, 512,
-                                smem_col<F>(P.c, P.clog, true), s>>>(
+                 k_col_inv2<F, 256><<<(R - qb + C - 1) / C, 256, sm, s>>>(
                      x, E, P.lr, (uint32_t)P.a, P.c, P.clog, qb, R,
                      P.b > 0 ? 1 : 0, omega_a_tw, rt));
     }
@@ -594,8 +603,7 @@ struct Launch {
                      x, E, P.lr, P.a, P.b, rt));
       const uint32_t qe = (uint32_t)P.b;
       TFT_LAUNCH(K_COL_INV,
-                 k_col_inv<F><<<(qe + C - 1) / C, 512,
-                                smem_col<F>(P.c, P.clog, true), s>>>(
+                 k_col_inv2<F, 256><<<(qe + C - 1) / C, 256, sm, s>>>(
                      x, E, P.lr, (uint32_t)(P.a + 1), P.c, P.clog, 0, qe, 0,
                      omega_a_tw, rt));
     }
@@ -635,15 +643,8 @@ struct Launch {
                      a, (uint32_t)na, b, (uint32_t)nb, out, P.l, rt));
       return cudaGetLastError();
     }
-    const uint32_t R = 1u << P.lr;
-    const uint32_t C = 1u << P.clog;
-    const size_t sc = smem_col<F>(P.c, P.clog, false);
-    TFT_LAUNCH(K_COL_FWD, k_col_fwd<F><<<(R + C - 1) / C, 512, sc, s>>>(
-                              a, na, out, EA, P.lr, P.a, P.b, P.c, P.clog, 0,
-                              R, rt));
-    TFT_LAUNCH(K_COL_FWD, k_col_fwd<F><<<(R + C - 1) / C, 512, sc, s>>>(
-                              b, nb, work, EB, P.lr, P.a, P.b, P.c, P.clog, 0,
-                              R, rt));
+    cols_fwd_v2(a, na, out, EA, P, rt, s, H);
+    cols_fwd_v2(b, nb, work, EB, P, rt, s, H);
     if (!use_v2(P)) {
       const uint64_t rows = P.a + (P.b ? 1 : 0);
       const uint32_t grid =
@@ -658,7 +659,7 @@ struct Launch {
       if (P.b > 0) {
         side.fork();
         cudaStream_t s2 = side.side();
-        TFT_LAUNCH_ON(K_ROW_MUL, s2,
+        TFT_LAUNCH_ON(K_LASTROW_MUL, s2,
                       k_row_mul<F><<<1, 512, smem_row<F>(P.lr, 2), s2>>>(
                           out, work, EA, EB, P.lr, P.a, P.b, 1, rt));
       }
@@ -685,60 +686,38 @@ static PlanSmem smem_of(const Plan& P) {
 }
 
 // ---------------------------------------------------------------------------
-// Prime dispatch
+// Per-field entry points, defined once per field in kernels_<field>.cu
+// (one translation unit per field so that they compile in parallel).
 // ---------------------------------------------------------------------------
-#define TFT_DISPATCH(prime, CALL)                          \
-  switch (prime) {                                         \
-    case 0: { using F = P998; CALL; }                      \
-    case 1: { using F = P2013; CALL; }                     \
-    case 2: { using F = Goldilocks; CALL; }                \
-    default: return cudaErrorInvalidValue;                 \
-  }
-
-cudaError_t prepare_kernels(int prime, size_t optin_smem) {
-  TFT_DISPATCH(prime, return Launch<F>::prepare(optin_smem));
-}
-
-cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
-                           void* E, const void* rt, int nsm, cudaStream_t s,
-                           const LaunchHook* hook, const AuxStreams* aux) {
-  TFT_DISPATCH(prime, return Launch<F>::forward(
-                          (typename F::T*)x, n, P, (typename F::T*)E,
-                          *(const RootTable<typename F::T>*)rt, nsm, s, hook,
-                          aux));
-}
-
-cudaError_t launch_inverse(int prime, void* x, uint64_t n, const Plan& P,
-                           void* E, uint64_t omega_a_tw, const void* rt,
-                           int nsm, cudaStream_t s, const LaunchHook* hook) {
-  TFT_DISPATCH(prime,
-               return Launch<F>::inverse(
-                   (typename F::T*)x, n, P, (typename F::T*)E,
-                   (typename F::T)omega_a_tw,
-                   *(const RootTable<typename F::T>*)rt, nsm, s, hook));
-}
-
-cudaError_t launch_polymul(int prime, const void* a, uint64_t na,
-                           const void* b, uint64_t nb, void* out,
-                           const Plan& P, void* work, void* EA, void* EB,
-                           uint64_t omega_a_tw, const void* rt, int nsm,
-                           cudaStream_t s, const LaunchHook* hook,
-                           const AuxStreams* aux) {
-  TFT_DISPATCH(prime,
-               return Launch<F>::polymul(
-                   (const typename F::T*)a, na, (const typename F::T*)b, nb,
-                   (typename F::T*)out, P, (typename F::T*)work,
-                   (typename F::T*)EA, (typename F::T*)EB,
-                   (typename F::T)omega_a_tw,
-                   *(const RootTable<typename F::T>*)rt, nsm, s, hook, aux));
-}
-
-PlanSmem plan_smem(int prime, const Plan& P) {
-  switch (prime) {
-    case 0: return smem_of<P998>(P);
-    case 1: return smem_of<P2013>(P);
-    default: return smem_of<Goldilocks>(P);
-  }
-}
+#define TFT_DEFINE_FIELD_ENTRIES(F, NAME)                                     \
+  cudaError_t NAME##_prepare(size_t optin) {                                  \
+    return Launch<F>::prepare(optin);                                         \
+  }                                                                           \
+  cudaError_t NAME##_forward(void* x, uint64_t n, const Plan& P, void* E,     \
+                             const void* rt, int nsm, cudaStream_t s,         \
+                             const LaunchHook* hook, const AuxStreams* aux) { \
+    return Launch<F>::forward((F::T*)x, n, P, (F::T*)E,                       \
+                              *(const RootTable<F::T>*)rt, nsm, s, hook,      \
+                              aux);                                           \
+  }                                                                           \
+  cudaError_t NAME##_inverse(void* x, uint64_t n, const Plan& P, void* E,     \
+                             uint64_t omega_a_tw, const void* rt, int nsm,    \
+                             cudaStream_t s, const LaunchHook* hook) {        \
+    return Launch<F>::inverse((F::T*)x, n, P, (F::T*)E, (F::T)omega_a_tw,     \
+                              *(const RootTable<F::T>*)rt, nsm, s, hook);     \
+  }                                                                           \
+  cudaError_t NAME##_polymul(const void* a, uint64_t na, const void* b,       \
+                             uint64_t nb, void* out, const Plan& P,           \
+                             void* work, void* EA, void* EB,                  \
+                             uint64_t omega_a_tw, const void* rt, int nsm,    \
+                             cudaStream_t s, const LaunchHook* hook,          \
+                             const AuxStreams* aux) {                         \
+    return Launch<F>::polymul((const F::T*)a, na, (const F::T*)b, nb,         \
+                              (F::T*)out, P, (F::T*)work, (F::T*)EA,          \
+                              (F::T*)EB, (F::T)omega_a_tw,                    \
+                              *(const RootTable<F::T>*)rt, nsm, s, hook,      \
+                              aux);                                           \
+  }                                                                           \
+  PlanSmem NAME##_plan_smem(const Plan& P) { return smem_of<F>(P); }
 
 }  // namespace tftgb

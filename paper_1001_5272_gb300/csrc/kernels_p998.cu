@@ -1,0 +1,6 @@
+// Kernels and launchers instantiated for one field (P998).
+#include "kernels_impl.cuh"
+
+namespace tftgb {
+TFT_DEFINE_FIELD_ENTRIES(P998, p998)
+}  // namespace tftgb

@@ -1,25 +1,42 @@
 // Row kernels on the register-blocked stage engine (stages.cuh).
 //
-// A row rho < a is block rho (2^lr positions) of the global network, so its
-// lr levels are run as stages with the twist zeta = omega_{rho 2^{lr-r_lo}} *
+// A row rho < a is block rho (2^LR positions) of the global network, so its
+// LR levels are run as stages with the twist zeta = omega_{rho 2^{LR-r_lo}} *
 // omega_{B_local 2^L}.  Each row is handled by R/16 threads holding 16
 // elements each; a CTA holds G = blockDim / (R/16) rows at a time.  The
-// kernels are persistent over rows.
+// kernels are persistent over rows and specialized on LR: the first stage
+// takes L0 = LR mod 4 levels (4 if that is 0), the others 4.
 #pragma once
 #include "stages.cuh"
 
 namespace tftgb {
 
-// Shared layout of the row kernels (after the static root table copy):
+template <int LR>
+struct RowGeom {
+  static constexpr uint32_t R = 1u << LR;
+  static constexpr int TPR = (int)(R >> 4);               // threads per row
+  static constexpr int THREADS = TPR < 256 ? 256 : TPR;   // per CTA
+  static constexpr int G = THREADS / TPR;                 // rows per CTA
+  // at least two CTAs per SM for 256-thread CTAs (caps registers at 128)
+  static constexpr int MIN_CTAS = THREADS <= 256 ? 2 : 1;
+  static constexpr int L0 = LR % 4 ? LR % 4 : 4;          // first stage
+  static constexpr int NST = 1 + (LR - L0) / 4;           // stages
+  // r_lo of stage si (stage 0 covers the top L0 levels)
+  static __host__ __device__ constexpr int r_lo(int si) {
+    return LR - L0 - 4 * si;
+  }
+};
+
+// Shared layout of the row kernels:
 //   K (StageConsts) | RF[G][2][5] | TL[tl] | TLi[tl] | Z[NB][G][R]
 template <class T>
 struct RowSmem {
   StageConsts<T>* K;
-  T* RF;    // RF[(g * 2 + inv) * 5 + stage]
+  T* RF;  // RF[(g * 2 + inv) * 5 + stage]
   T* TL;
   T* TLi;
   T* Z;
-  __device__ RowSmem(unsigned char* raw, int G, int tl, uint32_t R, int nbuf) {
+  __device__ RowSmem(unsigned char* raw, int G, int tl) {
     K = reinterpret_cast<StageConsts<T>*>(raw);
     T* p = reinterpret_cast<T*>(raw + sizeof(StageConsts<T>));
     RF = p;
@@ -28,11 +45,8 @@ struct RowSmem {
     p += tl;
     TLi = p;
     p += tl;
-    // align the data to 16 bytes
     uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
     Z = reinterpret_cast<T*>(a);
-    (void)R;
-    (void)nbuf;
   }
 };
 
@@ -42,6 +56,16 @@ __host__ __device__ inline size_t row_smem_bytes(int lr, int G, int nbuf) {
   size_t b = sizeof(StageConsts<T>) + sizeof(T) * (G * 10 + 2 * sp.tl_total);
   b = (b + 15) & ~(size_t)15;
   return b + sizeof(T) * ((size_t)nbuf * G << lr);
+}
+
+template <class F>
+__device__ void copy_roots(RootTable<typename F::T>* s_rt,
+                           const RootTable<typename F::T>& rt) {
+  using T = typename F::T;
+  const T* s = reinterpret_cast<const T*>(&rt);
+  T* d = reinterpret_cast<T*>(s_rt);
+  for (int i = threadIdx.x; i < (int)(sizeof(rt) / sizeof(T)); i += blockDim.x)
+    d[i] = s[i];
 }
 
 template <class F>
@@ -70,12 +94,11 @@ __device__ __forceinline__ void row_factors(RowSmem<typename F::T>& S,
 }
 
 // One forward stage on one operand of one row.  SRC_GLOBAL: read from Grow
-// (row in global memory), else from the swizzled shared row.
+// (the row in global memory), else from the swizzled shared row.
 template <class F, int L, bool SRC_GLOBAL>
 __device__ __forceinline__ void fwd_stage(typename F::T* Zrow,
                                           const typename F::T* Grow, int r_lo,
-                                          int t, int Tpr,
-                                          typename F::T RF,
+                                          int t, int Tpr, typename F::T RF,
                                           const typename F::T* TLs,
                                           const StageConsts<typename F::T>& K) {
   using T = typename F::T;
@@ -93,6 +116,42 @@ __device__ __forceinline__ void fwd_stage(typename F::T* Zrow,
     cnet_fwd<F, L>(x, K);
 #pragma unroll
     for (int i = 0; i < U; ++i) Zrow[swz(unit_pos(u, r_lo, L, i))] = x[i];
+  }
+}
+
+// One forward stage on both operands of the product (same rows, same twist):
+// the powers of zeta are computed once; operand B is processed after A has
+// been stored (the empty asm with a memory clobber keeps the compiler from
+// overlapping the two units, which would double the live registers).
+template <class F, int L, bool SRC_GLOBAL>
+__device__ __noinline__ void fwd_stage_ab(
+    typename F::T* ZA, const typename F::T* GA, typename F::T* ZB,
+    const typename F::T* GB, int r_lo, int t, int Tpr, typename F::T RF,
+    const typename F::T* TLs, const StageConsts<typename F::T>& K) {
+  using T = typename F::T;
+  constexpr int U = 1 << L;
+#pragma unroll 1
+  for (int v = 0; v < (16 >> L); ++v) {
+    const uint32_t u = (uint32_t)(v * Tpr + t);
+    T pw[U];
+    powers<F, L>(pw, F::mul_tw(RF, TLs[u >> r_lo]));
+#pragma unroll
+    for (int op = 0; op < 2; ++op) {
+      T* Zrow = op ? ZB : ZA;
+      const T* Grow = op ? GB : GA;
+      T x[U];
+#pragma unroll
+      for (int i = 0; i < U; ++i) {
+        const uint32_t p = unit_pos(u, r_lo, L, i);
+        x[i] = SRC_GLOBAL ? Grow[p] : Zrow[swz(p)];
+      }
+#pragma unroll
+      for (int i = 1; i < U; ++i) x[i] = F::mul_tw(x[i], pw[i]);
+      cnet_fwd<F, L>(x, K);
+#pragma unroll
+      for (int i = 0; i < U; ++i) Zrow[swz(unit_pos(u, r_lo, L, i))] = x[i];
+      asm volatile("" ::: "memory");
+    }
   }
 }
 
@@ -124,60 +183,48 @@ __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
   }
 }
 
-#define TFT_STAGE_SWITCH(L, CALL)          \
-  switch (L) {                             \
-    case 1: { constexpr int LL = 1; CALL; } break; \
-    case 2: { constexpr int LL = 2; CALL; } break; \
-    case 3: { constexpr int LL = 3; CALL; } break; \
-    default: { constexpr int LL = 4; CALL; } break; \
-  }
+// Common prologue of the row kernels: root table, constants, tables.
+#define TFT_ROW_PROLOGUE(NBUF)                                          \
+  using T = typename F::T;                                              \
+  using Geo = RowGeom<LR>;                                              \
+  extern __shared__ __align__(16) unsigned char smem_raw[];             \
+  __shared__ RootTable<T> s_rt;                                         \
+  copy_roots<F>(&s_rt, rt);                                             \
+  __syncthreads();                                                      \
+  constexpr uint32_t R = Geo::R;                                        \
+  constexpr int Tpr = Geo::TPR;                                         \
+  constexpr int G = Geo::G;                                             \
+  const int g = threadIdx.x / Tpr, t = threadIdx.x % Tpr;               \
+  const StagePlan sp = make_stage_plan(LR);                             \
+  RowSmem<T> S(smem_raw, G, sp.tl_total);                               \
+  row_setup<F>(S, sp, LR, s_rt);
 
 // ---------------------------------------------------------------------------
 // Forward rows rho < a.
 // ---------------------------------------------------------------------------
-template <class F, int MAXT>
-__global__ void __launch_bounds__(MAXT)
-k_row_fwd2(typename F::T* X, int lr, uint64_t a, RootTable<typename F::T> rt) {
-  using T = typename F::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ RootTable<T> s_rt;
-  {
-    const T* src = reinterpret_cast<const T*>(&rt);
-    T* dst = reinterpret_cast<T*>(&s_rt);
-    for (int i = threadIdx.x; i < (int)(sizeof(rt) / sizeof(T)); i += blockDim.x)
-      dst[i] = src[i];
-  }
-  __syncthreads();
-  const uint32_t R = 1u << lr;
-  const int Tpr = (int)(R >> 4);
-  const int G = blockDim.x / Tpr;
-  const int g = threadIdx.x / Tpr, t = threadIdx.x % Tpr;
-  const StagePlan sp = make_stage_plan(lr);
-  RowSmem<T> S(smem_raw, G, sp.tl_total, R, 1);
-  row_setup<F>(S, sp, lr, s_rt);
-  T* Zrow = S.Z + ((size_t)g << lr);
+template <class F, int LR>
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+k_row_fwd2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
+  TFT_ROW_PROLOGUE(1)
+  T* Zrow = S.Z + ((size_t)g << LR);
   for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
        rho0 += (uint64_t)gridDim.x * G) {
     const uint64_t rho = rho0 + g;
     const bool active = rho < a;
-    if (active) row_factors<F>(S, sp, lr, g, t, rho, s_rt);
+    if (active) row_factors<F>(S, sp, LR, g, t, rho, s_rt);
     __syncthreads();
     T* Grow = X + rho * R;
-    for (int si = 0; si < sp.n; ++si) {
-      if (active) {
-        const T RF = S.RF[(g * 2) * 5 + si];
-        const T* TLs = S.TL + sp.s[si].tl_off;
-        const int r_lo = sp.s[si].r_lo;
-        if (si == 0) {
-          TFT_STAGE_SWITCH(sp.s[si].L, (fwd_stage<F, LL, true>(
-                                           Zrow, Grow, r_lo, t, Tpr, RF, TLs,
-                                           *S.K)));
-        } else {
-          TFT_STAGE_SWITCH(sp.s[si].L, (fwd_stage<F, LL, false>(
-                                           Zrow, Grow, r_lo, t, Tpr, RF, TLs,
-                                           *S.K)));
-        }
-      }
+    if (active)
+      fwd_stage<F, Geo::L0, true>(Zrow, Grow, Geo::r_lo(0), t, Tpr,
+                                  S.RF[(g * 2) * 5], S.TL + sp.s[0].tl_off,
+                                  *S.K);
+    __syncthreads();
+#pragma unroll 1
+    for (int si = 1; si < Geo::NST; ++si) {
+      if (active)
+        fwd_stage<F, 4, false>(Zrow, Grow, Geo::r_lo(si), t, Tpr,
+                               S.RF[(g * 2) * 5 + si],
+                               S.TL + sp.s[si].tl_off, *S.K);
       __syncthreads();
     }
     if (active)
@@ -189,54 +236,34 @@ k_row_fwd2(typename F::T* X, int lr, uint64_t a, RootTable<typename F::T> rt) {
 // ---------------------------------------------------------------------------
 // Inverse rows rho < a.
 // ---------------------------------------------------------------------------
-template <class F, int MAXT>
-__global__ void __launch_bounds__(MAXT)
-k_row_inv2(typename F::T* X, int lr, uint64_t a, RootTable<typename F::T> rt) {
-  using T = typename F::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ RootTable<T> s_rt;
-  {
-    const T* src = reinterpret_cast<const T*>(&rt);
-    T* dst = reinterpret_cast<T*>(&s_rt);
-    for (int i = threadIdx.x; i < (int)(sizeof(rt) / sizeof(T)); i += blockDim.x)
-      dst[i] = src[i];
-  }
-  __syncthreads();
-  const uint32_t R = 1u << lr;
-  const int Tpr = (int)(R >> 4);
-  const int G = blockDim.x / Tpr;
-  const int g = threadIdx.x / Tpr, t = threadIdx.x % Tpr;
-  const StagePlan sp = make_stage_plan(lr);
-  RowSmem<T> S(smem_raw, G, sp.tl_total, R, 1);
-  row_setup<F>(S, sp, lr, s_rt);
-  T* Zrow = S.Z + ((size_t)g << lr);
+template <class F, int LR>
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
+  TFT_ROW_PROLOGUE(1)
+  T* Zrow = S.Z + ((size_t)g << LR);
   for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
        rho0 += (uint64_t)gridDim.x * G) {
     const uint64_t rho = rho0 + g;
     const bool active = rho < a;
     T* Grow = X + rho * R;
     if (active) {
-      row_factors<F>(S, sp, lr, g, t, rho, s_rt);
+      row_factors<F>(S, sp, LR, g, t, rho, s_rt);
       for (uint32_t q = t; q < R; q += Tpr) Zrow[swz(q)] = Grow[q];
     }
     __syncthreads();
-    for (int si = sp.n - 1; si >= 0; --si) {
-      if (active) {
-        const T RFi = S.RF[(g * 2 + 1) * 5 + si];
-        const T* TLis = S.TLi + sp.s[si].tl_off;
-        const int r_lo = sp.s[si].r_lo;
-        if (si == 0) {
-          TFT_STAGE_SWITCH(sp.s[si].L, (inv_stage<F, LL, true>(
-                                           Zrow, Grow, r_lo, t, Tpr, RFi,
-                                           TLis, *S.K)));
-        } else {
-          TFT_STAGE_SWITCH(sp.s[si].L, (inv_stage<F, LL, false>(
-                                           Zrow, Grow, r_lo, t, Tpr, RFi,
-                                           TLis, *S.K)));
-        }
-      }
+#pragma unroll 1
+    for (int si = Geo::NST - 1; si >= 1; --si) {
+      if (active)
+        inv_stage<F, 4, false>(Zrow, Grow, Geo::r_lo(si), t, Tpr,
+                               S.RF[(g * 2 + 1) * 5 + si],
+                               S.TLi + sp.s[si].tl_off, *S.K);
       __syncthreads();
     }
+    if (active)
+      inv_stage<F, Geo::L0, true>(Zrow, Grow, Geo::r_lo(0), t, Tpr,
+                                  S.RF[(g * 2 + 1) * 5],
+                                  S.TLi + sp.s[0].tl_off, *S.K);
+    __syncthreads();
   }
 }
 
@@ -244,61 +271,49 @@ k_row_inv2(typename F::T* X, int lr, uint64_t a, RootTable<typename F::T> rt) {
 // Fused product rows rho < a: forward row network of A' (in out) and B' (in
 // work), pointwise product, inverse row network, result to out.  The last
 // forward stage, the product and the first inverse stage share one unit in
-// registers.
+// registers.  Requires LR >= 8 (at least two stages).
 // ---------------------------------------------------------------------------
-template <class F, int MAXT>
-__global__ void __launch_bounds__(MAXT)
-k_row_mul2(typename F::T* out, const typename F::T* __restrict__ work, int lr,
+template <class F, int LR>
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+k_row_mul2(typename F::T* out, const typename F::T* __restrict__ work,
            uint64_t a, RootTable<typename F::T> rt) {
-  using T = typename F::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ RootTable<T> s_rt;
-  {
-    const T* src = reinterpret_cast<const T*>(&rt);
-    T* dst = reinterpret_cast<T*>(&s_rt);
-    for (int i = threadIdx.x; i < (int)(sizeof(rt) / sizeof(T)); i += blockDim.x)
-      dst[i] = src[i];
-  }
-  __syncthreads();
-  const uint32_t R = 1u << lr;
-  const int Tpr = (int)(R >> 4);
-  const int G = blockDim.x / Tpr;
-  const int g = threadIdx.x / Tpr, t = threadIdx.x % Tpr;
-  const StagePlan sp = make_stage_plan(lr);
-  RowSmem<T> S(smem_raw, G, sp.tl_total, R, 2);
-  row_setup<F>(S, sp, lr, s_rt);
-  T* ZA = S.Z + ((size_t)g << lr);
-  T* ZB = S.Z + ((size_t)(G + g) << lr);
-  const int last = sp.n - 1;  // the stage with r_lo = 0 (always L = 4)
+  TFT_ROW_PROLOGUE(2)
+  static_assert(Geo::NST >= 2, "fused row pass needs two stages");
+  T* ZA = S.Z + ((size_t)g << LR);
+  T* ZB = S.Z + ((size_t)(G + g) << LR);
+  constexpr int last = Geo::NST - 1;  // r_lo = 0, L = 4
   for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
        rho0 += (uint64_t)gridDim.x * G) {
     const uint64_t rho = rho0 + g;
     const bool active = rho < a;
-    if (active) row_factors<F>(S, sp, lr, g, t, rho, s_rt);
+    if (active) row_factors<F>(S, sp, LR, g, t, rho, s_rt);
     __syncthreads();
     T* GA = out + rho * R;
     const T* GB = work + rho * R;
-    // forward stages before the last, both operands
-    for (int si = 0; si < last; ++si) {
+    // both rows to shared memory (coalesced), then the first stage from
+    // there: reading the first stage straight from global memory lets the
+    // scheduler overlap the two operands' loads and spill registers
+    if (active) {
+      for (uint32_t q = t; q < R; q += Tpr) {
+        ZA[swz(q)] = GA[q];
+        ZB[swz(q)] = GB[q];
+      }
+    }
+    __syncthreads();
+    if (active) {
+      const T RF = S.RF[(g * 2) * 5];
+      const T* TLs = S.TL + sp.s[0].tl_off;
+      fwd_stage_ab<F, Geo::L0, false>(ZA, GA, ZB, GB, Geo::r_lo(0), t, Tpr,
+                                      RF, TLs, *S.K);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int si = 1; si < last; ++si) {
       if (active) {
         const T RF = S.RF[(g * 2) * 5 + si];
         const T* TLs = S.TL + sp.s[si].tl_off;
-        const int r_lo = sp.s[si].r_lo;
-        if (si == 0) {
-          TFT_STAGE_SWITCH(sp.s[si].L, (fwd_stage<F, LL, true>(
-                                           ZA, GA, r_lo, t, Tpr, RF, TLs,
-                                           *S.K)));
-          TFT_STAGE_SWITCH(sp.s[si].L, (fwd_stage<F, LL, true>(
-                                           ZB, GB, r_lo, t, Tpr, RF, TLs,
-                                           *S.K)));
-        } else {
-          TFT_STAGE_SWITCH(sp.s[si].L, (fwd_stage<F, LL, false>(
-                                           ZA, GA, r_lo, t, Tpr, RF, TLs,
-                                           *S.K)));
-          TFT_STAGE_SWITCH(sp.s[si].L, (fwd_stage<F, LL, false>(
-                                           ZB, GB, r_lo, t, Tpr, RF, TLs,
-                                           *S.K)));
-        }
+        fwd_stage_ab<F, 4, false>(ZA, GA, ZB, GB, Geo::r_lo(si), t, Tpr, RF,
+                                  TLs, *S.K);
       }
       __syncthreads();
     }
@@ -308,22 +323,23 @@ k_row_mul2(typename F::T* out, const typename F::T* __restrict__ work, int lr,
       const T RFi = S.RF[(g * 2 + 1) * 5 + last];
       const T* TLs = S.TL + sp.s[last].tl_off;
       const T* TLis = S.TLi + sp.s[last].tl_off;
-      const bool from_global = last == 0;
       const uint32_t u = (uint32_t)t;  // one unit per thread
       T xa[16], xb[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const uint32_t p = u * 16 + i;
-        xa[i] = from_global ? GA[p] : ZA[swz(p)];
-        xb[i] = from_global ? GB[p] : ZB[swz(p)];
+        xa[i] = ZA[swz(u * 16 + i)];
+        xb[i] = ZB[swz(u * 16 + i)];
       }
       {
-        T pw[16];
-        powers<F, 4>(pw, F::mul_tw(RF, TLs[u]));
+        // twist both operands with one running power (keeps register use
+        // at two units plus two words)
+        const T zeta = F::mul_tw(RF, TLs[u]);
+        T zp = zeta;
 #pragma unroll
         for (int i = 1; i < 16; ++i) {
-          xa[i] = F::mul_tw(xa[i], pw[i]);
-          xb[i] = F::mul_tw(xb[i], pw[i]);
+          xa[i] = F::mul_tw(xa[i], zp);
+          xb[i] = F::mul_tw(xb[i], zp);
+          if (i < 15) zp = F::mul_tw(zp, zeta);
         }
       }
       cnet_fwd<F, 4>(xa, *S.K);
@@ -333,33 +349,35 @@ k_row_mul2(typename F::T* out, const typename F::T* __restrict__ work, int lr,
       cnet_inv<F, 4>(xa, *S.K);
       twist<F, 4>(xa, F::mul_tw(RFi, TLis[u]));
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        if (last == 0)
-          GA[u * 16 + i] = xa[i];
-        else
-          ZA[swz(u * 16 + i)] = xa[i];
-      }
+      for (int i = 0; i < 16; ++i) ZA[swz(u * 16 + i)] = xa[i];
     }
     __syncthreads();
-    // remaining inverse stages
-    for (int si = last - 1; si >= 0; --si) {
-      if (active) {
-        const T RFi = S.RF[(g * 2 + 1) * 5 + si];
-        const T* TLis = S.TLi + sp.s[si].tl_off;
-        const int r_lo = sp.s[si].r_lo;
-        if (si == 0) {
-          TFT_STAGE_SWITCH(sp.s[si].L, (inv_stage<F, LL, true>(
-                                           ZA, GA, r_lo, t, Tpr, RFi, TLis,
-                                           *S.K)));
-        } else {
-          TFT_STAGE_SWITCH(sp.s[si].L, (inv_stage<F, LL, false>(
-                                           ZA, GA, r_lo, t, Tpr, RFi, TLis,
-                                           *S.K)));
-        }
-      }
+#pragma unroll 1
+    for (int si = last - 1; si >= 1; --si) {
+      if (active)
+        inv_stage<F, 4, false>(ZA, GA, Geo::r_lo(si), t, Tpr,
+                               S.RF[(g * 2 + 1) * 5 + si],
+                               S.TLi + sp.s[si].tl_off, *S.K);
       __syncthreads();
     }
+    if (active)
+      inv_stage<F, Geo::L0, true>(ZA, GA, Geo::r_lo(0), t, Tpr,
+                                  S.RF[(g * 2 + 1) * 5],
+                                  S.TLi + sp.s[0].tl_off, *S.K);
+    __syncthreads();
   }
 }
+
+// Dispatch a runtime lr in [8, 14] to a compile-time LR.
+#define TFT_LR_DISPATCH(lr, ...)                        \
+  switch (lr) {                                         \
+    case 8: { constexpr int LR = 8; __VA_ARGS__; } break; \
+    case 9: { constexpr int LR = 9; __VA_ARGS__; } break; \
+    case 10: { constexpr int LR = 10; __VA_ARGS__; } break; \
+    case 11: { constexpr int LR = 11; __VA_ARGS__; } break; \
+    case 12: { constexpr int LR = 12; __VA_ARGS__; } break; \
+    case 13: { constexpr int LR = 13; __VA_ARGS__; } break; \
+    default: { constexpr int LR = 14; __VA_ARGS__; } break; \
+  }
 
 }  // namespace tftgb

@@ -175,6 +175,15 @@ __device__ __forceinline__ void twist(typename F::T (&x)[1 << L],
   for (int i = 1; i < (1 << L); ++i) x[i] = F::mul_tw(x[i], pw[i]);
 }
 
+// Dispatch a runtime stage width L in [1, 4] to a compile-time LL.
+#define TFT_STAGE_SWITCH(L, ...)                                \
+  switch (L) {                                                  \
+    case 1: { constexpr int LL = 1; __VA_ARGS__; } break;       \
+    case 2: { constexpr int LL = 2; __VA_ARGS__; } break;       \
+    case 3: { constexpr int LL = 3; __VA_ARGS__; } break;       \
+    default: { constexpr int LL = 4; __VA_ARGS__; } break;      \
+  }
+
 // Unit geometry of a stage.
 __device__ __forceinline__ uint32_t unit_pos(uint32_t u, int r_lo, int L,
                                              int i) {

@@ -17,7 +17,9 @@ enum KernelKind {
   K_COL_INV = 5,
   K_LASTROW_INV = 6,
   K_ROW_MUL = 7,
-  K_NUM_KINDS = 8
+  K_LASTROW_FWD = 8,   // ragged last row of a forward transform
+  K_LASTROW_MUL = 9,   // ragged last row of a product (forward + pointwise)
+  K_NUM_KINDS = 10
 };
 
 // Called around every kernel launch (may be null).

@@ -270,7 +270,7 @@ def tft_last_error(ctx):
     return int(load().tft_last_error(ctx.handle))
 
 
-NUM_KERNEL_KINDS = 8
+NUM_KERNEL_KINDS = 10
 
 
 def kernel_name(kind):
