@@ -128,6 +128,66 @@ tft_status tft_polymul(tft_ctx* ctx, const void* a, uint64_t na,
                        const void* b, uint64_t nb, void* out, void* stream);
 
 /*
+ * Batched products: many independent polymul(a, b) calls (Section 5's
+ * product, each exactly as tft_polymul computes it) in a few launches.
+ *
+ * Products with r = na + nb - 1 <= 2^small_log run one per CTA entirely in
+ * shared memory; the others use the row/column split with one row length
+ * 2^lr for all of them, as six launches that each cover every large product
+ * (forward columns, fused rows, last rows, inverse short columns, inverse
+ * last rows, inverse long columns).  Each launch is persistent over its task
+ * list.
+ *
+ * Usage: tft_ctx_reserve_batch once (reserves the descriptor tables for up
+ * to max_products and a work area of work_words elements: each large
+ * product needs r + 2 * 2^lr elements of it, see tft_batch_work_words);
+ * tft_batch_plan for a set of products (validates, classifies, uploads the
+ * tables; synchronous, not capturable); tft_batch_run to launch the planned
+ * batch on a stream (launches only, so it can be captured into a CUDA
+ * graph and replayed; the operands may change between runs, the pointers
+ * and lengths may not).  tft_polymul_batch = plan + run.
+ *
+ * Each descriptor: a, b (device, read only, na, nb >= 1 elements), out
+ * (device, r elements, not overlapping a or b); 16-byte aligned.  Errors:
+ * TFT_EINVAL (bad descriptor or parameters, no reservation), TFT_ERANGE
+ * (more products than reserved, work area too small, or a product too long
+ * for the row length: its 2^c column rows, c = ceil(log2(ceil(r / 2^lr))),
+ * must satisfy c <= 13 (32-bit primes) or 12 (2^64 - 2^32 + 1), and a tile
+ * of 2^(c + clog) elements must fit in the device's shared memory -- with
+ * 16 columns of 4-byte elements that is c <= 11, i.e. r <= 2^(lr + 11)).
+ */
+typedef struct tft_polymul_desc {
+  const void* a;
+  uint64_t na;
+  const void* b;
+  uint64_t nb;
+  void* out;
+} tft_polymul_desc;
+
+/* Batch schedule; 0 in a field means the default (32-bit primes:
+ * small_log 13, lr 9, 16 columns per tile; 2^64 - 2^32 + 1: 12, 10, 4).
+ * Constraints: 8 <= lr <= 12, lr <= small_log <= 13 (12 for 64-bit
+ * elements), columns per tile 2^(clog_plus1 - 1) <= 16. */
+typedef struct tft_batch_params {
+  uint32_t small_log;
+  uint32_t lr;
+  uint32_t clog_plus1;
+  uint32_t reserved;
+} tft_batch_params;
+
+tft_status tft_ctx_reserve_batch(tft_ctx* ctx, uint32_t max_products,
+                                 uint64_t work_words);
+tft_status tft_batch_work_words(tft_prime prime, const tft_polymul_desc* descs,
+                                uint32_t count, const tft_batch_params* params,
+                                uint64_t* words);
+tft_status tft_batch_plan(tft_ctx* ctx, const tft_polymul_desc* descs,
+                          uint32_t count, const tft_batch_params* params);
+tft_status tft_batch_run(tft_ctx* ctx, void* stream);
+tft_status tft_polymul_batch(tft_ctx* ctx, const tft_polymul_desc* descs,
+                             uint32_t count, const tft_batch_params* params,
+                             void* stream);
+
+/*
  * tft_forward_noalloc: the in-place forward TFT of tft_forward, for callers
  * that must not allocate device memory and so cannot create a context --
  * for example a serving loop whose device memory is fully reserved at

@@ -1,0 +1,238 @@
+// Batched TFT products: many independent products in a handful of launches.
+//
+// Products are split into two size classes by r = na + nb - 1:
+//   small (r <= 2^small_log): one CTA holds both operands in shared memory
+//          (the single-CTA product), one product per task;
+//   large: the row/column split with one row length R = 2^lr for the whole
+//          class (a_p, b_p, c_p per product), run as six phase launches over
+//          all large products: forward columns of both operands, fused rows,
+//          ragged last rows, inverse short columns (+ E_q), inverse last
+//          rows, inverse long columns.
+// Every kernel is persistent over its flattened task list (task -> product
+// by a prefix table), so one launch per phase covers the whole batch and the
+// launch sequence can be captured into one CUDA graph.
+#pragma once
+#include "cols.cuh"
+#include "engine.cuh"
+#include "rows.cuh"
+
+namespace tftgb {
+
+struct BatchSmall {
+  uint64_t a, b, out;  // device pointers
+  uint32_t na, nb;
+  uint32_t l;          // log2 of the padded length (r <= 2^l)
+  uint32_t pad;
+};
+
+struct BatchLarge {
+  uint64_t a, b, out, work, EA, EB;  // device pointers
+  uint64_t na, nb;
+  uint64_t omega_a_tw;               // omega_{a_p} in twiddle form
+  uint32_t A;                        // a_p = r >> lr (full rows)
+  uint32_t Bm;                       // b_p = r mod R (last row length)
+  uint32_t c;                        // columns padded to 2^c
+  uint32_t pad;
+  uint64_t row_base;                 // prefix of A over products
+  uint64_t cs_base;                  // prefix of short-column tiles
+  uint64_t cl_base;                  // prefix of long-column tiles
+};
+
+// Largest p with base(p) <= x over a non-decreasing prefix (binary search).
+template <class Get>
+__device__ __forceinline__ uint32_t find_product(uint32_t n, uint64_t x,
+                                                 Get base) {
+  uint32_t lo = 0, hi = n;  // invariant: base(lo) <= x < base(hi)
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (base(mid) <= x)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Small class: one product per CTA at a time (single-CTA product of
+// kernels_impl.cuh: operands interleaved as two columns, pruned forward
+// network, pointwise product, generalized block inverse).
+// ---------------------------------------------------------------------------
+template <class F>
+__global__ void __launch_bounds__(512)
+k_small_mul_batch(const BatchSmall* __restrict__ d, uint32_t n, int lmax,
+                  RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  stage_roots<F>(&s_rt, rt);
+  const uint32_t NMAX = 1u << lmax;
+  T* Z = reinterpret_cast<T*>(smem_raw);  // 2 NMAX
+  T* W = Z + 2 * NMAX;
+  T* Wih = W + (NMAX > 1 ? NMAX / 2 : 1);
+  for (uint32_t p = blockIdx.x; p < n; p += gridDim.x) {
+    const BatchSmall q = d[p];
+    const int l = (int)q.l;
+    const uint32_t N = 1u << l;
+    const uint32_t r = q.na + q.nb - 1;
+    const T* A = reinterpret_cast<const T*>(q.a);
+    const T* B = reinterpret_cast<const T*>(q.b);
+    T* out = reinterpret_cast<T*>(q.out);
+    __syncthreads();  // the previous product is done with shared memory
+    build_base_tables<F>(W, Wih, l, s_rt);
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+      Z[2 * i] = i < q.na ? A[i] : T(0);
+      Z[2 * i + 1] = i < q.nb ? B[i] : T(0);
+    }
+    __syncthreads();
+    ColTw<F> tw{W, Wih};
+    fwd_pruned<F>(Z, 1, 1, l, r, tw);
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
+      Z[2 * i] = i < r ? F::mul_data(Z[2 * i], Z[2 * i + 1]) : T(0);
+    __syncthreads();
+    inv_block<F>(Z, 0, 1, l, r, tw);
+    for (uint32_t i = threadIdx.x; i < r; i += blockDim.x) out[i] = Z[2 * i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Large class, phase 1: forward column pass of both operands of every
+// product.  Task = (product, operand, column tile of C columns).
+// ---------------------------------------------------------------------------
+template <class F>
+__global__ void __launch_bounds__(256)
+k_col_fwd_batch(const BatchLarge* __restrict__ d, uint32_t nl, int lr,
+                int clog, RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  stage_roots<F>(&s_rt, rt);
+  const uint32_t R = 1u << lr;
+  const uint32_t tiles = R >> clog;
+  const uint64_t total = (uint64_t)nl * 2 * tiles;
+  for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
+    const uint32_t p = (uint32_t)(task / (2 * tiles));
+    const uint32_t o = (uint32_t)((task / tiles) & 1);
+    const uint32_t j = (uint32_t)(task % tiles);
+    const BatchLarge q = d[p];
+    const T* src = reinterpret_cast<const T*>(o ? q.b : q.a);
+    T* dst = reinterpret_cast<T*>(o ? q.work : q.out);
+    T* E = reinterpret_cast<T*>(o ? q.EB : q.EA);
+    col_fwd_tile<F>(smem_raw, s_rt, src, o ? q.nb : q.na, dst, E, lr, q.A,
+                    q.Bm, (int)q.c, clog, j << clog, R);
+  }
+}
+
+// Phase 2: fused rows, all full rows of all products flattened.
+template <class F, int LR>
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+k_row_mul_batch(const BatchLarge* __restrict__ d, uint32_t nl,
+                uint64_t total_rows, RootTable<typename F::T> rt) {
+  TFT_ROW_PROLOGUE(2)
+  for (uint64_t row0 = (uint64_t)blockIdx.x * G; row0 < total_rows;
+       row0 += (uint64_t)gridDim.x * G) {
+    const uint64_t row = row0 + g;
+    const bool active = row < total_rows;
+    uint64_t rho = 0;
+    T* GA = nullptr;
+    const T* GB = nullptr;
+    if (active) {
+      const uint32_t p =
+          find_product(nl, row, [&](uint32_t i) { return d[i].row_base; });
+      rho = row - d[p].row_base;
+      GA = reinterpret_cast<T*>(d[p].out) + rho * R;
+      GB = reinterpret_cast<const T*>(d[p].work) + rho * R;
+    }
+    row_mul_body<F, LR>(S, sp, g, t, active, rho, GA, GB, s_rt);
+  }
+}
+
+// Phase 3: ragged last rows (forward of both operands + pointwise).
+template <class F, int LR>
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+k_row_last_batch(const BatchLarge* __restrict__ d, uint32_t nl,
+                 RootTable<typename F::T> rt) {
+  TFT_ROW_PROLOGUE(2)
+  for (uint32_t p0 = blockIdx.x * G; p0 < nl; p0 += gridDim.x * G) {
+    const uint32_t p = p0 + g;
+    const bool active = p < nl && d[p].Bm > 0;
+    uint64_t rho = 0;
+    uint32_t bm = 0;
+    T* GA = nullptr;
+    const T *EA = nullptr, *GB = nullptr, *EB = nullptr;
+    if (active) {
+      const BatchLarge q = d[p];
+      rho = q.A;
+      bm = q.Bm;
+      GA = reinterpret_cast<T*>(q.out) + rho * R;
+      EA = reinterpret_cast<const T*>(q.EA);
+      GB = reinterpret_cast<const T*>(q.work) + rho * R;
+      EB = reinterpret_cast<const T*>(q.EB);
+    }
+    row_last_body<F, LR, true>(S, sp, g, t, active, rho, bm, GA, EA, GB, EB,
+                               s_rt);
+  }
+}
+
+// Phases 4 and 6: inverse columns.  long_cols = 0: short columns [b_p, R)
+// of length a_p, with E_q; long_cols = 1: long columns [0, b_p) of length
+// a_p + 1.  Task = (product, tile) through the prefix cs_base / cl_base.
+template <class F>
+__global__ void __launch_bounds__(256)
+k_col_inv_batch(const BatchLarge* __restrict__ d, uint32_t nl,
+                uint64_t total, int lr, int clog, int long_cols,
+                RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  stage_roots<F>(&s_rt, rt);
+  const uint32_t R = 1u << lr;
+  const uint32_t C = 1u << clog;
+  for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
+    const uint32_t p = find_product(nl, task, [&](uint32_t i) {
+      return long_cols ? d[i].cl_base : d[i].cs_base;
+    });
+    const BatchLarge q = d[p];
+    const uint32_t j =
+        (uint32_t)(task - (long_cols ? q.cl_base : q.cs_base));
+    const uint32_t q0 = (long_cols ? 0u : q.Bm) + j * C;
+    const uint32_t q_end = long_cols ? q.Bm : R;
+    col_inv_tile<F>(smem_raw, s_rt, reinterpret_cast<T*>(q.out),
+                    reinterpret_cast<T*>(q.EA), lr, long_cols ? q.A + 1 : q.A,
+                    (int)q.c, clog, q0, q_end,
+                    (!long_cols && q.Bm > 0) ? 1 : 0, (T)q.omega_a_tw);
+  }
+}
+
+// Phase 5: inverse last rows (generalized block inverse of block a_p with
+// the E_q as known inputs), one product per CTA at a time.
+template <class F>
+__global__ void __launch_bounds__(512)
+k_lastrow_inv_batch(const BatchLarge* __restrict__ d, uint32_t nl, int lr,
+                    RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  stage_roots<F>(&s_rt, rt);
+  const uint32_t R = 1u << lr;
+  T* Z = reinterpret_cast<T*>(smem_raw);
+  T* W = Z + R;
+  T* Wih = W + R / 2;
+  T* L = Wih + R / 2;
+  build_base_tables<F>(W, Wih, lr, s_rt);
+  for (uint32_t p = blockIdx.x; p < nl; p += gridDim.x) {
+    const BatchLarge q = d[p];
+    if (q.Bm == 0) continue;  // uniform across the CTA
+    T* row = reinterpret_cast<T*>(q.out) + (uint64_t)q.A * R;
+    const T* E = reinterpret_cast<const T*>(q.EA);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < R; i += blockDim.x)
+      Z[i] = i < q.Bm ? row[i] : E[i];
+    __syncthreads();
+    RowTw<F> tw{W, Wih, L, &s_rt, q.A, lr};
+    inv_block<F>(Z, 0, 0, lr, q.Bm, tw);
+    for (uint32_t i = threadIdx.x; i < q.Bm; i += blockDim.x) row[i] = Z[i];
+  }
+}
+
+}  // namespace tftgb

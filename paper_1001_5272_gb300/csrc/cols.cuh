@@ -112,22 +112,15 @@ __device__ __forceinline__ void col_fwd_stage(
 // writes straight to global memory: rows t < a to dst, row a to dst for long
 // columns (q < b) and to E for short ones.
 // ---------------------------------------------------------------------------
-template <class F, int MAXT>
-__global__ void __launch_bounds__(MAXT)
-k_col_fwd2(const typename F::T* src, uint64_t n_src, typename F::T* dst,
-           typename F::T* __restrict__ E, int lr, uint64_t a, uint64_t b,
-           int c, int clog, uint32_t q_begin, uint32_t q_end,
-           RootTable<typename F::T> rt) {
+template <class F>
+__device__ void col_fwd_tile(unsigned char* smem_raw,
+                             const RootTable<typename F::T>& s_rt,
+                             const typename F::T* src, uint64_t n_src,
+                             typename F::T* dst, typename F::T* E, int lr,
+                             uint64_t a, uint64_t b, int c, int clog,
+                             uint32_t q0, uint32_t q_end) {
   using T = typename F::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ RootTable<T> s_rt;
-  {
-    const T* s = reinterpret_cast<const T*>(&rt);
-    T* d = reinterpret_cast<T*>(&s_rt);
-    for (int i = threadIdx.x; i < (int)(sizeof(rt) / sizeof(T)); i += blockDim.x)
-      d[i] = s[i];
-  }
-  __syncthreads();
+  __syncthreads();  // the previous tile is done with shared memory
   const StagePlan sp = make_stage_plan(c);
   ColSmem<T> S(smem_raw, sp.tl_total);
   for (int i = threadIdx.x; i < 8; i += blockDim.x) {
@@ -137,7 +130,6 @@ k_col_fwd2(const typename F::T* src, uint64_t n_src, typename F::T* dst,
   build_stage_tables<F>(S.TL, S.TLi, sp, c, s_rt);
   __syncthreads();
   const uint64_t R = 1ull << lr;
-  const uint32_t q0 = q_begin + blockIdx.x * (1u << clog);
   const uint32_t rows = (uint32_t)(a + (b > 0 ? 1 : 0));
   for (int si = 0; si < sp.n; ++si) {
     const int r_lo = sp.s[si].r_lo;
@@ -160,6 +152,32 @@ k_col_fwd2(const typename F::T* src, uint64_t n_src, typename F::T* dst,
 #undef TFT_COL_FWD_CALL
     __syncthreads();
   }
+}
+
+// Per-CTA copy of the root table (kernel parameters are not addressable
+// without a local copy).
+template <class F>
+__device__ __forceinline__ void stage_roots(RootTable<typename F::T>* s_rt,
+                                            const RootTable<typename F::T>& rt) {
+  using T = typename F::T;
+  const T* s = reinterpret_cast<const T*>(&rt);
+  T* d = reinterpret_cast<T*>(s_rt);
+  for (int i = threadIdx.x; i < (int)(sizeof(rt) / sizeof(T)); i += blockDim.x)
+    d[i] = s[i];
+  __syncthreads();
+}
+
+template <class F, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+k_col_fwd2(const typename F::T* src, uint64_t n_src, typename F::T* dst,
+           typename F::T* __restrict__ E, int lr, uint64_t a, uint64_t b,
+           int c, int clog, uint32_t q_begin, uint32_t q_end,
+           RootTable<typename F::T> rt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<typename F::T> s_rt;
+  stage_roots<F>(&s_rt, rt);
+  col_fwd_tile<F>(smem_raw, s_rt, src, n_src, dst, E, lr, a, b, c, clog,
+                  q_begin + blockIdx.x * (1u << clog), q_end);
 }
 
 // omega_{2j} (twiddle form) as the product of omega_[b+2] over the set bits b
@@ -243,22 +261,15 @@ __device__ __forceinline__ void col_inv_stage_flat(
 // stage engine.  With want_E also E_q = C_q(omega_a) by a parallel Horner
 // rule (omega_a in twiddle form).
 // ---------------------------------------------------------------------------
-template <class F, int MAXT>
-__global__ void __launch_bounds__(MAXT)
-k_col_inv2(typename F::T* X, typename F::T* __restrict__ E, int lr,
-           uint32_t m, int c, int clog, uint32_t q_begin, uint32_t q_end,
-           int want_E, typename F::T omega_a_tw,
-           RootTable<typename F::T> rt) {
+template <class F>
+__device__ void col_inv_tile(unsigned char* smem_raw,
+                             const RootTable<typename F::T>& s_rt,
+                             typename F::T* X, typename F::T* E, int lr,
+                             uint32_t m, int c, int clog, uint32_t q0,
+                             uint32_t q_end, int want_E,
+                             typename F::T omega_a_tw) {
   using T = typename F::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ RootTable<T> s_rt;
-  {
-    const T* s = reinterpret_cast<const T*>(&rt);
-    T* d = reinterpret_cast<T*>(&s_rt);
-    for (int i = threadIdx.x; i < (int)(sizeof(rt) / sizeof(T)); i += blockDim.x)
-      d[i] = s[i];
-  }
-  __syncthreads();
+  __syncthreads();  // the previous tile is done with shared memory
   // stage tables for 4-level stages: TL16[m'] = omega_{16 m'}, m' < 2^{c-4}
   const StagePlan sp = make_stage_plan(c);
   ColSmem<T> S(smem_raw, sp.tl_total);
@@ -281,7 +292,6 @@ k_col_inv2(typename F::T* X, typename F::T* __restrict__ E, int lr,
   }
   const uint32_t C = 1u << clog;
   const uint64_t R = 1ull << lr;
-  const uint32_t q0 = q_begin + blockIdx.x * C;
   const uint32_t N = 1u << c;
   T* Z = S.Z;
   for (uint32_t i = threadIdx.x; i < (N << clog); i += blockDim.x) {
@@ -427,6 +437,20 @@ k_col_inv2(typename F::T* X, typename F::T* __restrict__ E, int lr,
       if (q < q_end) E[q] = sacc;
     }
   }
+}
+
+template <class F, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+k_col_inv2(typename F::T* X, typename F::T* __restrict__ E, int lr,
+           uint32_t m, int c, int clog, uint32_t q_begin, uint32_t q_end,
+           int want_E, typename F::T omega_a_tw,
+           RootTable<typename F::T> rt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<typename F::T> s_rt;
+  stage_roots<F>(&s_rt, rt);
+  col_inv_tile<F>(smem_raw, s_rt, X, E, lr, m, c, clog,
+                  q_begin + blockIdx.x * (1u << clog), q_end, want_E,
+                  omega_a_tw);
 }
 
 }  // namespace tftgb

@@ -17,7 +17,11 @@ namespace tftgb {
                              uint64_t omega_a_tw, const void* rt, int nsm,    \
                              cudaStream_t s, const LaunchHook* hook,          \
                              const AuxStreams* aux);                          \
-  PlanSmem NAME##_plan_smem(const Plan& P);
+  PlanSmem NAME##_plan_smem(const Plan& P);                                   \
+  cudaError_t NAME##_batch(const BatchLaunch& B, const void* rt, int nsm,   \
+                           cudaStream_t s, const LaunchHook* hook,          \
+                           const AuxStreams* aux);                          \
+  cudaError_t NAME##_prepare_batch(size_t optin);
 
 TFT_FIELD_DECLS(p998)
 TFT_FIELD_DECLS(p2013)
@@ -32,8 +36,16 @@ TFT_FIELD_DECLS(gold)
   }
 
 cudaError_t prepare_kernels(int prime, size_t optin) {
-  TFT_BY_PRIME(prime, p998_prepare(optin), p2013_prepare(optin),
-               gold_prepare(optin));
+  cudaError_t e;
+  switch (prime) {
+    case 0: e = p998_prepare(optin); break;
+    case 1: e = p2013_prepare(optin); break;
+    case 2: e = gold_prepare(optin); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  TFT_BY_PRIME(prime, p998_prepare_batch(optin), p2013_prepare_batch(optin),
+               gold_prepare_batch(optin));
 }
 
 cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
@@ -65,6 +77,14 @@ cudaError_t launch_polymul(int prime, const void* a, uint64_t na,
                              rt, nsm, s, hook, aux),
                gold_polymul(a, na, b, nb, out, P, work, EA, EB, omega_a_tw,
                             rt, nsm, s, hook, aux));
+}
+
+cudaError_t launch_batch(int prime, const BatchLaunch& B, const void* rt,
+                         int nsm, cudaStream_t s, const LaunchHook* hook,
+                         const AuxStreams* aux) {
+  TFT_BY_PRIME(prime, p998_batch(B, rt, nsm, s, hook, aux),
+               p2013_batch(B, rt, nsm, s, hook, aux),
+               gold_batch(B, rt, nsm, s, hook, aux));
 }
 
 PlanSmem plan_smem(int prime, const Plan& P) {

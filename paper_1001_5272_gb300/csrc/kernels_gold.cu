@@ -1,4 +1,5 @@
-// Kernels and launchers instantiated for one field (Goldilocks).
+// Kernels and launchers instantiated for one field (Goldilocks): single products
+// and transforms.
 #include "kernels_impl.cuh"
 
 namespace tftgb {

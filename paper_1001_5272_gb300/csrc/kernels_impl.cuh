@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "engine.cuh"
+#include "batch.cuh"
 #include "cols.cuh"
 #include "rows.cuh"
 #include "tft_internal.h"
@@ -434,12 +435,17 @@ struct Launch {
     if ((e = set_smem<F>((const void*)k_row_fwd2<F, LRV>, mx))) return e;  \
     if ((e = set_smem<F>((const void*)k_row_inv2<F, LRV>, mx))) return e;  \
     if ((e = set_smem<F>((const void*)k_row_mul2<F, LRV>, mx))) return e;  \
+    if ((e = set_smem<F>((const void*)k_row_last2<F, LRV, false>, mx)))    \
+      return e;                                                            \
+    if ((e = set_smem<F>((const void*)k_row_last2<F, LRV, true>, mx)))     \
+      return e;                                                            \
   } while (0)
 
   static cudaError_t prepare(size_t mx) {
     cudaError_t e;
     if ((e = set_smem<F>((const void*)k_col_fwd2<F, 256>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_col_inv2<F, 256>, mx))) return e;
+
     if ((e = set_smem<F>((const void*)k_small<F, false>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_small<F, true>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_small_mul<F>, mx))) return e;
@@ -574,9 +580,16 @@ struct Launch {
     if (P.b > 0) {
       side.fork();
       cudaStream_t s2 = side.side();
-      TFT_LAUNCH_ON(K_LASTROW_FWD, s2,
-                    k_row_fwd<F><<<1, 512, smem_row<F>(P.lr, 0), s2>>>(
-                        x, E, P.lr, P.a, P.b, 1, rt));
+      TFT_LR_DISPATCH(P.lr, {
+        using Geo = RowGeom<LR>;
+        TFT_LAUNCH_ON(K_LASTROW_FWD, s2,
+                      (k_row_last2<F, LR, false><<<1, Geo::THREADS,
+                                                   row_smem_bytes<T>(LR, Geo::G,
+                                                                     1),
+                                                   s2>>>(x, E, nullptr,
+                                                         nullptr, P.a, P.b,
+                                                         rt)));
+      });
     }
     cudaError_t e = rows_fwd_v2(x, P, rt, nsm, s, H);
     if (P.b > 0) side.join();
@@ -659,15 +672,126 @@ struct Launch {
       if (P.b > 0) {
         side.fork();
         cudaStream_t s2 = side.side();
-        TFT_LAUNCH_ON(K_LASTROW_MUL, s2,
-                      k_row_mul<F><<<1, 512, smem_row<F>(P.lr, 2), s2>>>(
-                          out, work, EA, EB, P.lr, P.a, P.b, 1, rt));
+        TFT_LR_DISPATCH(P.lr, {
+          using Geo = RowGeom<LR>;
+          TFT_LAUNCH_ON(K_LASTROW_MUL, s2,
+                        (k_row_last2<F, LR, true><<<1, Geo::THREADS,
+                                                    row_smem_bytes<T>(
+                                                        LR, Geo::G, 2),
+                                                    s2>>>(out, EA, work, EB,
+                                                          P.a, P.b, rt)));
+        });
       }
       cudaError_t e = rows_mul_v2(out, work, P, rt, nsm, s, H);
       if (P.b > 0) side.join();
       if (e != cudaSuccess) return e;
     }
     return inverse_tail(out, P, EA, omega_a_tw, rt, s, H);
+  }
+  // Persistent grid: the SMs times the resident CTAs of `kernel`.
+  template <class K>
+  static uint32_t persistent_grid(K kernel, int threads, size_t smem,
+                                  uint64_t tasks, int nsm) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads,
+                                                      smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    const uint64_t cap = (uint64_t)nsm * per_sm;
+    return (uint32_t)(tasks < cap ? (tasks ? tasks : 1) : cap);
+  }
+
+  static cudaError_t prepare_batch(size_t mx) {
+    cudaError_t e;
+    if ((e = set_smem<F>((const void*)k_small_mul_batch<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_col_fwd_batch<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_col_inv_batch<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_lastrow_inv_batch<F>, mx))) return e;
+#define TFT_PREP_BATCH_LR(LRV)                                             \
+  if ((e = set_smem<F>((const void*)k_row_mul_batch<F, LRV>, mx))) return e; \
+  if ((e = set_smem<F>((const void*)k_row_last_batch<F, LRV>, mx))) return e;
+    TFT_PREP_BATCH_LR(8)
+    TFT_PREP_BATCH_LR(9)
+    TFT_PREP_BATCH_LR(10)
+    TFT_PREP_BATCH_LR(11)
+    TFT_PREP_BATCH_LR(12)
+#undef TFT_PREP_BATCH_LR
+    return cudaSuccess;
+  }
+
+  // A planned batch: the small class on the side stream, the six phases of
+  // the large class on the caller's stream.
+  static cudaError_t batch(const BatchLaunch& B, const RT& rt, int nsm,
+                           cudaStream_t s, const LaunchHook* H,
+                           const AuxStreams* aux) {
+    const SideRow side{aux, s};
+    if (B.ns) {
+      side.fork();
+      cudaStream_t s2 = side.side();
+      const size_t sm = smem_small_mul<F>(B.lmax);
+      const uint32_t grid =
+          persistent_grid(k_small_mul_batch<F>, 512, sm, B.ns, nsm);
+      TFT_LAUNCH_ON(K_SMALL_MUL, s2,
+                    (k_small_mul_batch<F><<<grid, 512, sm, s2>>>(
+                        (const BatchSmall*)B.small, B.ns, B.lmax, rt)));
+    }
+    if (B.nl) {
+      const BatchLarge* d = (const BatchLarge*)B.large;
+      const uint32_t R = 1u << B.lr;
+      const size_t smc = col_smem_bytes<T>(B.cmax, B.clog);
+      const uint64_t fwd_tasks = (uint64_t)B.nl * 2 * (R >> B.clog);
+      TFT_LAUNCH(K_COL_FWD,
+                 (k_col_fwd_batch<F><<<persistent_grid(k_col_fwd_batch<F>,
+                                                       256, smc, fwd_tasks,
+                                                       nsm),
+                                       256, smc, s>>>(d, B.nl, B.lr, B.clog,
+                                                      rt)));
+      TFT_LR_DISPATCH_BATCH(B.lr, {
+        using Geo = RowGeom<LR>;
+        const size_t smr = row_smem_bytes<T>(LR, Geo::G, 2);
+        const uint64_t slots = (B.total_rows + Geo::G - 1) / Geo::G;
+        TFT_LAUNCH(K_ROW_MUL,
+                   (k_row_mul_batch<F, LR><<<persistent_grid(
+                                                 k_row_mul_batch<F, LR>,
+                                                 Geo::THREADS, smr, slots,
+                                                 nsm),
+                                             Geo::THREADS, smr, s>>>(
+                       d, B.nl, B.total_rows, rt)));
+        const uint64_t lslots = (B.nl + Geo::G - 1) / Geo::G;
+        TFT_LAUNCH(K_LASTROW_MUL,
+                   (k_row_last_batch<F, LR><<<persistent_grid(
+                                                  k_row_last_batch<F, LR>,
+                                                  Geo::THREADS, smr, lslots,
+                                                  nsm),
+                                              Geo::THREADS, smr, s>>>(
+                       d, B.nl, rt)));
+      });
+      if (B.cs_tiles)
+        TFT_LAUNCH(K_COL_INV,
+                   (k_col_inv_batch<F><<<persistent_grid(k_col_inv_batch<F>,
+                                                         256, smc, B.cs_tiles,
+                                                         nsm),
+                                         256, smc, s>>>(d, B.nl, B.cs_tiles,
+                                                        B.lr, B.clog, 0,
+                                                        rt)));
+      const size_t sml = smem_row<F>(B.lr, 1);
+      TFT_LAUNCH(K_LASTROW_INV,
+                 (k_lastrow_inv_batch<F><<<persistent_grid(
+                                               k_lastrow_inv_batch<F>, 512,
+                                               sml, B.nl, nsm),
+                                           512, sml, s>>>(d, B.nl, B.lr,
+                                                          rt)));
+      if (B.cl_tiles)
+        TFT_LAUNCH(K_COL_INV,
+                   (k_col_inv_batch<F><<<persistent_grid(k_col_inv_batch<F>,
+                                                         256, smc, B.cl_tiles,
+                                                         nsm),
+                                         256, smc, s>>>(d, B.nl, B.cl_tiles,
+                                                        B.lr, B.clog, 1,
+                                                        rt)));
+    }
+    if (B.ns) side.join();
+    return cudaGetLastError();
   }
 };
 
@@ -719,5 +843,16 @@ static PlanSmem smem_of(const Plan& P) {
                               aux);                                           \
   }                                                                           \
   PlanSmem NAME##_plan_smem(const Plan& P) { return smem_of<F>(P); }
+
+#define TFT_DEFINE_FIELD_BATCH(F, NAME)                                       \
+  cudaError_t NAME##_prepare_batch(size_t optin) {                            \
+    return Launch<F>::prepare_batch(optin);                                   \
+  }                                                                           \
+  cudaError_t NAME##_batch(const BatchLaunch& B, const void* rt, int nsm,     \
+                           cudaStream_t s, const LaunchHook* hook,            \
+                           const AuxStreams* aux) {                           \
+    return Launch<F>::batch(B, *(const RootTable<F::T>*)rt, nsm, s, hook,     \
+                            aux);                                             \
+  }
 
 }  // namespace tftgb

@@ -1,4 +1,5 @@
-// Kernels and launchers instantiated for one field (P2013).
+// Kernels and launchers instantiated for one field (P2013): single products
+// and transforms.
 #include "kernels_impl.cuh"
 
 namespace tftgb {

@@ -268,105 +268,218 @@ k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
 }
 
 // ---------------------------------------------------------------------------
-// Fused product rows rho < a: forward row network of A' (in out) and B' (in
-// work), pointwise product, inverse row network, result to out.  The last
-// forward stage, the product and the first inverse stage share one unit in
-// registers.  Requires LR >= 8 (at least two stages).
+// Fused product rows: forward row network of A' and B', pointwise product,
+// inverse row network, result written over A'.  The last forward stage, the
+// product and the first inverse stage share one unit in registers.  Requires
+// LR >= 8 (at least two stages).  row_mul_body processes, for every row slot
+// g of the CTA, row rho_g (GA, GB: that row of A' and B' in global memory);
+// inactive slots only take part in the barriers.
 // ---------------------------------------------------------------------------
+template <class F, int LR>
+__device__ __forceinline__ void row_mul_body(
+    RowSmem<typename F::T>& S, const StagePlan& sp, int g, int t,
+    bool active, uint64_t rho, typename F::T* GA,
+    const typename F::T* GB, const RootTable<typename F::T>& s_rt) {
+  using T = typename F::T;
+  using Geo = RowGeom<LR>;
+  constexpr uint32_t R = Geo::R;
+  constexpr int Tpr = Geo::TPR;
+  constexpr int G = Geo::G;
+  static_assert(Geo::NST >= 2, "fused row pass needs two stages");
+  T* ZA = S.Z + ((size_t)g << LR);
+  T* ZB = S.Z + ((size_t)(G + g) << LR);
+  constexpr int last = Geo::NST - 1;  // r_lo = 0, L = 4
+  if (active) row_factors<F>(S, sp, LR, g, t, rho, s_rt);
+  __syncthreads();
+  // both rows to shared memory (coalesced), then the first stage from
+  // there: reading the first stage straight from global memory lets the
+  // scheduler overlap the two operands' loads and spill registers
+  if (active) {
+    for (uint32_t q = t; q < R; q += Tpr) {
+      ZA[swz(q)] = GA[q];
+      ZB[swz(q)] = GB[q];
+    }
+  }
+  __syncthreads();
+  if (active) {
+    const T RF = S.RF[(g * 2) * 5];
+    const T* TLs = S.TL + sp.s[0].tl_off;
+    fwd_stage_ab<F, Geo::L0, false>(ZA, GA, ZB, GB, Geo::r_lo(0), t, Tpr,
+                                    RF, TLs, *S.K);
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int si = 1; si < last; ++si) {
+    if (active) {
+      const T RF = S.RF[(g * 2) * 5 + si];
+      const T* TLs = S.TL + sp.s[si].tl_off;
+      fwd_stage_ab<F, 4, false>(ZA, GA, ZB, GB, Geo::r_lo(si), t, Tpr, RF,
+                                TLs, *S.K);
+    }
+    __syncthreads();
+  }
+  // last forward stage (r_lo = 0, L = 4) + product + first inverse stage
+  if (active) {
+    const T RF = S.RF[(g * 2) * 5 + last];
+    const T RFi = S.RF[(g * 2 + 1) * 5 + last];
+    const T* TLs = S.TL + sp.s[last].tl_off;
+    const T* TLis = S.TLi + sp.s[last].tl_off;
+    const uint32_t u = (uint32_t)t;  // one unit per thread
+    T xa[16], xb[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      xa[i] = ZA[swz(u * 16 + i)];
+      xb[i] = ZB[swz(u * 16 + i)];
+    }
+    {
+      // twist both operands with one running power (keeps register use
+      // at two units plus two words)
+      const T zeta = F::mul_tw(RF, TLs[u]);
+      T zp = zeta;
+#pragma unroll
+      for (int i = 1; i < 16; ++i) {
+        xa[i] = F::mul_tw(xa[i], zp);
+        xb[i] = F::mul_tw(xb[i], zp);
+        if (i < 15) zp = F::mul_tw(zp, zeta);
+      }
+    }
+    cnet_fwd<F, 4>(xa, *S.K);
+    cnet_fwd<F, 4>(xb, *S.K);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) xa[i] = F::mul_data(xa[i], xb[i]);
+    cnet_inv<F, 4>(xa, *S.K);
+    twist<F, 4>(xa, F::mul_tw(RFi, TLis[u]));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) ZA[swz(u * 16 + i)] = xa[i];
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int si = last - 1; si >= 1; --si) {
+    if (active)
+      inv_stage<F, 4, false>(ZA, GA, Geo::r_lo(si), t, Tpr,
+                             S.RF[(g * 2 + 1) * 5 + si],
+                             S.TLi + sp.s[si].tl_off, *S.K);
+    __syncthreads();
+  }
+  if (active)
+    inv_stage<F, Geo::L0, true>(ZA, GA, Geo::r_lo(0), t, Tpr,
+                                S.RF[(g * 2 + 1) * 5],
+                                S.TLi + sp.s[0].tl_off, *S.K);
+  __syncthreads();
+}
+
 template <class F, int LR>
 __global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
 k_row_mul2(typename F::T* out, const typename F::T* __restrict__ work,
            uint64_t a, RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE(2)
-  static_assert(Geo::NST >= 2, "fused row pass needs two stages");
-  T* ZA = S.Z + ((size_t)g << LR);
-  T* ZB = S.Z + ((size_t)(G + g) << LR);
-  constexpr int last = Geo::NST - 1;  // r_lo = 0, L = 4
   for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
        rho0 += (uint64_t)gridDim.x * G) {
     const uint64_t rho = rho0 + g;
-    const bool active = rho < a;
-    if (active) row_factors<F>(S, sp, LR, g, t, rho, s_rt);
-    __syncthreads();
-    T* GA = out + rho * R;
-    const T* GB = work + rho * R;
-    // both rows to shared memory (coalesced), then the first stage from
-    // there: reading the first stage straight from global memory lets the
-    // scheduler overlap the two operands' loads and spill registers
-    if (active) {
-      for (uint32_t q = t; q < R; q += Tpr) {
-        ZA[swz(q)] = GA[q];
-        ZB[swz(q)] = GB[q];
-      }
+    row_mul_body<F, LR>(S, sp, g, t, rho < a, rho, out + rho * R,
+                        work + rho * R, s_rt);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The ragged last row (block a, first b outputs) on the stage engine: the
+// full forward network of block a, whose inputs are the long columns' last
+// entries (q < b, in the buffer) and E_q (q >= b, scratch).  TWO: product
+// (both operands, then the pointwise product); else a forward transform.
+// Only outputs q < b are stored, over the row's first b words.
+// ---------------------------------------------------------------------------
+template <class F, int LR, bool TWO>
+__device__ __forceinline__ void row_last_body(
+    RowSmem<typename F::T>& S, const StagePlan& sp, int g, int t,
+    bool active, uint64_t rho, uint32_t b, typename F::T* GA,
+    const typename F::T* EA, const typename F::T* GB,
+    const typename F::T* EB, const RootTable<typename F::T>& s_rt) {
+  using T = typename F::T;
+  using Geo = RowGeom<LR>;
+  constexpr uint32_t R = Geo::R;
+  constexpr int Tpr = Geo::TPR;
+  constexpr int G = Geo::G;
+  T* ZA = S.Z + ((size_t)g << LR);
+  T* ZB = S.Z + ((size_t)(G + g) << LR);
+  constexpr int last = Geo::NST - 1;
+  if (active) row_factors<F>(S, sp, LR, g, t, rho, s_rt);
+  if (active) {
+    for (uint32_t q = t; q < R; q += Tpr) {
+      ZA[swz(q)] = q < b ? GA[q] : EA[q];
+      if (TWO) ZB[swz(q)] = q < b ? GB[q] : EB[q];
     }
-    __syncthreads();
-    if (active) {
-      const T RF = S.RF[(g * 2) * 5];
-      const T* TLs = S.TL + sp.s[0].tl_off;
-      fwd_stage_ab<F, Geo::L0, false>(ZA, GA, ZB, GB, Geo::r_lo(0), t, Tpr,
-                                      RF, TLs, *S.K);
-    }
-    __syncthreads();
+  }
+  __syncthreads();
 #pragma unroll 1
-    for (int si = 1; si < last; ++si) {
-      if (active) {
-        const T RF = S.RF[(g * 2) * 5 + si];
-        const T* TLs = S.TL + sp.s[si].tl_off;
-        fwd_stage_ab<F, 4, false>(ZA, GA, ZB, GB, Geo::r_lo(si), t, Tpr, RF,
-                                  TLs, *S.K);
-      }
-      __syncthreads();
-    }
-    // last forward stage (r_lo = 0, L = 4) + product + first inverse stage
+  for (int si = 0; si < last; ++si) {
     if (active) {
-      const T RF = S.RF[(g * 2) * 5 + last];
-      const T RFi = S.RF[(g * 2 + 1) * 5 + last];
-      const T* TLs = S.TL + sp.s[last].tl_off;
-      const T* TLis = S.TLi + sp.s[last].tl_off;
-      const uint32_t u = (uint32_t)t;  // one unit per thread
-      T xa[16], xb[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        xa[i] = ZA[swz(u * 16 + i)];
-        xb[i] = ZB[swz(u * 16 + i)];
+      const T RF = S.RF[(g * 2) * 5 + si];
+      const T* TLs = S.TL + sp.s[si].tl_off;
+      const int r_lo = Geo::r_lo(si);
+      if (si == 0) {
+        if (TWO)
+          fwd_stage_ab<F, Geo::L0, false>(ZA, GA, ZB, GB, r_lo, t, Tpr, RF,
+                                          TLs, *S.K);
+        else
+          fwd_stage<F, Geo::L0, false>(ZA, GA, r_lo, t, Tpr, RF, TLs, *S.K);
+      } else {
+        if (TWO)
+          fwd_stage_ab<F, 4, false>(ZA, GA, ZB, GB, r_lo, t, Tpr, RF, TLs,
+                                    *S.K);
+        else
+          fwd_stage<F, 4, false>(ZA, GA, r_lo, t, Tpr, RF, TLs, *S.K);
       }
-      {
-        // twist both operands with one running power (keeps register use
-        // at two units plus two words)
-        const T zeta = F::mul_tw(RF, TLs[u]);
-        T zp = zeta;
+    }
+    __syncthreads();
+  }
+  if (active) {
+    const T RF = S.RF[(g * 2) * 5 + last];
+    const T* TLs = S.TL + sp.s[last].tl_off;
+    const uint32_t u = (uint32_t)t;  // 16 consecutive outputs per thread
+    T xa[16];
 #pragma unroll
-        for (int i = 1; i < 16; ++i) {
-          xa[i] = F::mul_tw(xa[i], zp);
-          xb[i] = F::mul_tw(xb[i], zp);
-          if (i < 15) zp = F::mul_tw(zp, zeta);
-        }
-      }
-      cnet_fwd<F, 4>(xa, *S.K);
+    for (int i = 0; i < 16; ++i) xa[i] = ZA[swz(u * 16 + i)];
+    const T zeta = F::mul_tw(RF, TLs[u]);
+    twist<F, 4>(xa, zeta);
+    cnet_fwd<F, 4>(xa, *S.K);
+    if (TWO) {
+      T xb[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) xb[i] = ZB[swz(u * 16 + i)];
+      twist<F, 4>(xb, zeta);
       cnet_fwd<F, 4>(xb, *S.K);
 #pragma unroll
       for (int i = 0; i < 16; ++i) xa[i] = F::mul_data(xa[i], xb[i]);
-      cnet_inv<F, 4>(xa, *S.K);
-      twist<F, 4>(xa, F::mul_tw(RFi, TLis[u]));
+    }
 #pragma unroll
-      for (int i = 0; i < 16; ++i) ZA[swz(u * 16 + i)] = xa[i];
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int si = last - 1; si >= 1; --si) {
-      if (active)
-        inv_stage<F, 4, false>(ZA, GA, Geo::r_lo(si), t, Tpr,
-                               S.RF[(g * 2 + 1) * 5 + si],
-                               S.TLi + sp.s[si].tl_off, *S.K);
-      __syncthreads();
-    }
-    if (active)
-      inv_stage<F, Geo::L0, true>(ZA, GA, Geo::r_lo(0), t, Tpr,
-                                  S.RF[(g * 2 + 1) * 5],
-                                  S.TLi + sp.s[0].tl_off, *S.K);
-    __syncthreads();
+    for (int i = 0; i < 16; ++i)
+      if (u * 16 + i < b) GA[u * 16 + i] = xa[i];
   }
+  __syncthreads();
 }
+
+// Last row of one transform (TWO = false) or product (TWO = true).
+template <class F, int LR, bool TWO>
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+k_row_last2(typename F::T* X, const typename F::T* __restrict__ E,
+            const typename F::T* work, const typename F::T* __restrict__ EB,
+            uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
+  TFT_ROW_PROLOGUE(TWO ? 2 : 1)
+  // one row: slot 0 of the first CTA
+  row_last_body<F, LR, TWO>(S, sp, g, t, blockIdx.x == 0 && g == 0, a,
+                            (uint32_t)b, X + a * R, E,
+                            TWO ? work + a * R : nullptr, EB, s_rt);
+}
+
+// Dispatch a runtime lr in [8, 12] (the batched large class) to LR.
+#define TFT_LR_DISPATCH_BATCH(lr, ...)                           \
+  switch (lr) {                                                  \
+    case 8: { constexpr int LR = 8; __VA_ARGS__; } break;        \
+    case 9: { constexpr int LR = 9; __VA_ARGS__; } break;        \
+    case 10: { constexpr int LR = 10; __VA_ARGS__; } break;      \
+    case 11: { constexpr int LR = 11; __VA_ARGS__; } break;      \
+    default: { constexpr int LR = 12; __VA_ARGS__; } break;      \
+  }
 
 // Dispatch a runtime lr in [8, 14] to a compile-time LR.
 #define TFT_LR_DISPATCH(lr, ...)                        \

@@ -62,6 +62,25 @@ struct AuxStreams {
   cudaEvent_t join;
 };
 
+// A planned batch of products (tables already on the device).
+struct BatchLaunch {
+  const void* small;   // BatchSmall[ns] on the device
+  uint32_t ns;
+  int lmax;            // largest small-class log length
+  const void* large;   // BatchLarge[nl] on the device
+  uint32_t nl;
+  int lr;              // row length of the large class
+  int clog;            // columns per tile
+  int cmax;            // largest column log length
+  uint64_t total_rows; // sum of a_p
+  uint64_t cs_tiles;   // inverse short-column tiles
+  uint64_t cl_tiles;   // inverse long-column tiles
+};
+
+cudaError_t launch_batch(int prime, const BatchLaunch& B, const void* rt,
+                         int nsm, cudaStream_t s, const LaunchHook* hook,
+                         const AuxStreams* aux);
+
 cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
                            void* E, const void* rt, int nsm, cudaStream_t s,
                            const LaunchHook* hook, const AuxStreams* aux);

@@ -29,6 +29,19 @@ TFT_CTX_HOST_STAGING = 1
 _lib = None
 
 
+class PolymulDesc(ctypes.Structure):
+    """tft_polymul_desc: one product of a batch (device pointers)."""
+    _fields_ = [("a", ctypes.c_void_p), ("na", ctypes.c_uint64),
+                ("b", ctypes.c_void_p), ("nb", ctypes.c_uint64),
+                ("out", ctypes.c_void_p)]
+
+
+class BatchParams(ctypes.Structure):
+    """tft_batch_params: 0 in a field selects the library default."""
+    _fields_ = [("small_log", ctypes.c_uint32), ("lr", ctypes.c_uint32),
+                ("clog_plus1", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 class TFTError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -71,6 +84,15 @@ def load():
         "tft_kernel_name": (ctypes.c_char_p, [i32]),
         "tft_launch_count": (u64, [vp]),
         "tft_forward_noalloc": (i32, [i32, vp, u64, u32, vp]),
+        "tft_ctx_reserve_batch": (i32, [vp, u32, u64]),
+        "tft_batch_work_words": (i32, [i32, ctypes.POINTER(PolymulDesc), u32,
+                                       ctypes.POINTER(BatchParams),
+                                       ctypes.POINTER(u64)]),
+        "tft_batch_plan": (i32, [vp, ctypes.POINTER(PolymulDesc), u32,
+                                 ctypes.POINTER(BatchParams)]),
+        "tft_batch_run": (i32, [vp, vp]),
+        "tft_polymul_batch": (i32, [vp, ctypes.POINTER(PolymulDesc), u32,
+                                    ctypes.POINTER(BatchParams), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -311,3 +333,74 @@ def tft_forward_noalloc(prime, x, k=None, stream=None):
                                  n, k, _stream_handle(stream)),
            "tft_forward_noalloc")
     return x
+
+
+# ---------------------------------------------------------------------------
+# Batched products
+# ---------------------------------------------------------------------------
+
+def _descs(products, elem_bytes):
+    """products: sequence of (a, b, out) CUDA tensors."""
+    arr = (PolymulDesc * max(1, len(products)))()
+    for i, (a, b, out) in enumerate(products):
+        if out.numel() != a.numel() + b.numel() - 1:
+            raise ValueError(f"product {i}: out must have len(a)+len(b)-1 "
+                             "elements")
+        arr[i].a = _dev_ptr(a, elem_bytes, "a").value
+        arr[i].na = a.numel()
+        arr[i].b = _dev_ptr(b, elem_bytes, "b").value
+        arr[i].nb = b.numel()
+        arr[i].out = _dev_ptr(out, elem_bytes, "out").value
+    return arr
+
+
+def _params(params):
+    if params is None:
+        return None
+    if isinstance(params, BatchParams):
+        return ctypes.byref(params)
+    p = BatchParams()
+    p.small_log = int(params.get("small_log", 0))
+    p.lr = int(params.get("lr", 0))
+    clog = params.get("clog")
+    p.clog_plus1 = 0 if clog is None else int(clog) + 1
+    return ctypes.byref(p)
+
+
+def tft_ctx_reserve_batch(ctx, max_products, work_words):
+    _check(load().tft_ctx_reserve_batch(ctx.handle, int(max_products),
+                                        int(work_words)),
+           "tft_ctx_reserve_batch")
+
+
+def tft_batch_work_words(prime, lengths, params=None):
+    """Work-area elements a batch of (na, nb) pairs needs."""
+    arr = (PolymulDesc * max(1, len(lengths)))()
+    for i, (na, nb) in enumerate(lengths):
+        arr[i].na, arr[i].nb = int(na), int(nb)
+    w = ctypes.c_uint64()
+    _check(load().tft_batch_work_words(prime_id(prime), arr, len(lengths),
+                                       _params(params), ctypes.byref(w)),
+           "tft_batch_work_words")
+    return w.value
+
+
+def tft_batch_plan(ctx, products, params=None):
+    """Plan a batch of (a, b, out) CUDA tensors (uploads the tables)."""
+    _check(load().tft_batch_plan(ctx.handle, _descs(products, ctx.elem_bytes),
+                                 len(products), _params(params)),
+           "tft_batch_plan")
+
+
+def tft_batch_run(ctx, stream=None):
+    """Launch the planned batch (capturable into a CUDA graph)."""
+    _check(load().tft_batch_run(ctx.handle, _stream_handle(stream)),
+           "tft_batch_run")
+
+
+def tft_polymul_batch(ctx, products, params=None, stream=None):
+    _check(load().tft_polymul_batch(ctx.handle,
+                                    _descs(products, ctx.elem_bytes),
+                                    len(products), _params(params),
+                                    _stream_handle(stream)),
+           "tft_polymul_batch")

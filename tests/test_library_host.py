@@ -97,3 +97,47 @@ def test_context_creation_without_gpu_fails_cleanly():
     st = L.tft_ctx_create(2, 0, 1024, 0, ctypes.byref(h))
     assert st in (tft.TFT_ECUDA, tft.TFT_EINVAL)
     assert not h.value
+
+
+@pytest.mark.parametrize("pid", [0, 1, 2])
+def test_batch_work_words(pid):
+    # host-only sizing of the batched product's work area: each product of
+    # the row/column class takes r words for B' plus two R-word E buffers,
+    # each slot rounded up to 16 bytes; the single-CTA class takes none
+    w = 8 if pid == 2 else 4
+    small_log, lr = (12, 10) if w == 8 else (13, 9)
+    al = 16 // w
+
+    def up(x):
+        return (x + al - 1) // al * al
+
+    rng = __import__("random").Random(pid)
+    pairs = [(1, 1), (1 << (small_log - 1), (1 << (small_log - 1)) + 1),
+             (1 << (small_log - 1), (1 << (small_log - 1)) + 2),
+             (65536, 65536)] + [(rng.randint(1, 40000), rng.randint(1, 40000))
+                                for _ in range(20)]
+    expect = 0
+    for na, nb in pairs:
+        r = na + nb - 1
+        if r > (1 << small_log):
+            expect += up(r) + 2 * up(1 << lr)
+    assert tft.tft_batch_work_words(pid, pairs) == expect
+    # an explicit schedule: everything above 2^8 in the row/column class
+    expect8 = sum(up(na + nb - 1) + 2 * up(1 << 8) for na, nb in pairs
+                  if na + nb - 1 > 256)
+    assert tft.tft_batch_work_words(pid, pairs,
+                                    {"lr": 8, "small_log": 8}) == expect8
+    assert tft.tft_batch_work_words(pid, []) == 0
+    with pytest.raises(tft.TFTError):
+        tft.tft_batch_work_words(pid, [(0, 5)])
+
+
+def test_batch_entry_points_reject_null_context():
+    L = tft.load()
+    assert L.tft_ctx_reserve_batch(None, 4, 100) == tft.TFT_EINVAL
+    assert L.tft_batch_plan(None, None, 0, None) == tft.TFT_EINVAL
+    assert L.tft_batch_run(None, None) == tft.TFT_EINVAL
+    assert L.tft_polymul_batch(None, None, 0, None, None) == tft.TFT_EINVAL
+    w = ctypes.c_uint64()
+    assert L.tft_batch_work_words(7, None, 0, None, ctypes.byref(w)) == \
+        tft.TFT_EINVAL
