@@ -66,7 +66,14 @@ def parse_args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the single-transform and e2e legs")
+                    help="skip the single-transform, e2e and batched legs")
+    ap.add_argument("--only", choices=("batched",),
+                    help="run one leg alone and print its JSON (profiling)")
+    ap.add_argument("--batch-count", type=int, default=None,
+                    help="products in the batched leg (default 4096)")
+    ap.add_argument("--batch-params", default=None,
+                    help="small_log,lr,clog for the batched leg "
+                         "(default: autotuned)")
     return ap.parse_args()
 
 
@@ -413,6 +420,9 @@ def run_ours(args):
                "ms_per_step": 1e3 * statistics.mean(e2e_s),
                "matches_device_result": same}
 
+        extra["batched_p2013265921_4096"] = batched_leg(args, tft, dev,
+                                                        steps)
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, cores, desc, _ = oracle_polymul_sample(scale=0.125)
@@ -450,10 +460,112 @@ def run_ours(args):
     return 0
 
 
+def pack_aligned(arrays, align):
+    """Concatenate 1-D arrays into one buffer, each starting at a multiple
+    of ``align`` elements (16-byte aligned operands); returns the buffer and
+    the offsets."""
+    import numpy as np
+    offs, pos = [], 0
+    for x in arrays:
+        offs.append(pos)
+        pos += (x.size + align - 1) // align * align
+    buf = np.zeros(pos, dtype=arrays[0].dtype)
+    for o, x in zip(offs, arrays):
+        buf[o:o + x.size] = x
+    return buf, offs
+
+
+def batched_leg(args, tft, dev, steps):
+    """4096 independent products over 2013265921, lengths log-uniform in
+    [64, 65536]: schedule autotuned on the batch, the planned launches
+    captured into one CUDA graph, Sum r / time over graph replays.  The
+    operands (about 300 MB) and outputs exceed L2, so no flush is needed."""
+    import numpy as np
+    import torch
+
+    from paper_1001_5272_gb300 import autotune
+    from workloads import config4_inputs
+
+    A, B = config4_inputs(args.batch_count)
+    na = np.array([a.size for a in A])
+    nb = np.array([b.size for b in B])
+    r = na + nb - 1
+    abuf, aoff = pack_aligned([a.astype(np.uint32) for a in A], 4)
+    bbuf, boff = pack_aligned([b.astype(np.uint32) for b in B], 4)
+    _, ooff = pack_aligned([np.empty(int(x), np.uint32) for x in r], 4)
+    ta = torch.from_numpy(abuf.view(np.int32)).to(dev)
+    tb = torch.from_numpy(bbuf.view(np.int32)).to(dev)
+    tout = torch.empty(ooff[-1] + int(r[-1]) + 4, dtype=torch.int32,
+                       device=dev)
+    prods = [(ta[aoff[i]:aoff[i] + na[i]], tb[boff[i]:boff[i] + nb[i]],
+              tout[ooff[i]:ooff[i] + r[i]]) for i in range(len(A))]
+    ctx = tft.Context(1, dev, max_len=int(r.max()))
+    if args.batch_params:
+        sl, lr, cl = (int(v) for v in args.batch_params.split(","))
+        params, table = {"small_log": sl, "lr": lr, "clog": cl}, {}
+        tft.tft_ctx_reserve_batch(
+            ctx, len(prods),
+            tft.tft_batch_work_words(1, list(zip(na, nb)), params))
+    else:
+        params, table = autotune.tune_batch(ctx, prods, use_cache=False)
+    tft.tft_batch_plan(ctx, prods, params)
+    # per-kernel shares from one profiled run outside the graph
+    tft.tft_profile_enable(ctx, True)
+    l0 = tft.tft_launch_count(ctx)
+    tft.tft_batch_run(ctx)
+    torch.cuda.synchronize()
+    launches_per_run = tft.tft_launch_count(ctx) - l0
+    prof = tft.tft_profile_read(ctx)
+    tft.tft_profile_enable(ctx, False)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        tft.tft_batch_run(ctx, s)
+        s.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            tft.tft_batch_run(ctx, s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps)]
+    cur = torch.cuda.current_stream()
+    for i in range(steps):
+        ev[2 * i].record(cur)
+        g.replay()
+        ev[2 * i + 1].record(cur)
+    torch.cuda.synchronize()
+    ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(steps)]
+    # spot check against the single-call path on a few products
+    ok = True
+    for i in (0, 1, len(A) // 2, len(A) - 1):
+        o = torch.empty(int(r[i]), dtype=torch.int32, device=dev)
+        tft.tft_polymul(ctx, prods[i][0], prods[i][1], o)
+        ok &= bool(torch.equal(o, prods[i][2]))
+    ctx.close()
+    sum_r = int(r.sum())
+    mean_ms = statistics.mean(ms)
+    return {"products": len(A), "sum_r": sum_r,
+            "ms_per_batch": mean_ms, "ms_min": min(ms),
+            "mcoeffs": sum_r / mean_ms / 1e3,
+            "params": params, "tuned_over": len(table),
+            "launches_per_batch": launches_per_run,
+            "graph": "all launches of one batch captured in one CUDA graph",
+            "kernels_ms": {k: v[0] for k, v in prof.items()},
+            "matches_single_calls": ok}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only == "batched":
+        import torch
+        from paper_1001_5272_gb300 import tft
+        torch.cuda.set_device(0)
+        out = batched_leg(args, tft, 0, max(1, args.steps))
+        print(json.dumps({"leg": "batched_p2013265921", **out}), flush=True)
+        return 0
     return run_ours(args)
 
 

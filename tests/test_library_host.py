@@ -141,3 +141,19 @@ def test_batch_entry_points_reject_null_context():
     w = ctypes.c_uint64()
     assert L.tft_batch_work_words(7, None, 0, None, ctypes.byref(w)) == \
         tft.TFT_EINVAL
+
+
+def test_autotune_grid_is_admissible():
+    # every candidate schedule satisfies the constraints tft_batch_plan
+    # checks, and the sizing entry point accepts it
+    from paper_1001_5272_gb300 import autotune
+    for pid in (0, 1, 2):
+        grid = autotune.candidates(pid)
+        assert grid
+        for g in grid:
+            assert 8 <= g["lr"] <= 12
+            assert g["lr"] <= g["small_log"] <= (12 if pid == 2 else 13)
+            assert 0 <= g["clog"] <= 4
+            tft.tft_batch_work_words(pid, [(5000, 7000)], g)
+    assert autotune.mix_signature([(1, 1), (2, 3), (3, 2), (64, 65)]) == \
+        "0:1,2:2,7:1"
