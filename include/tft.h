@@ -188,6 +188,106 @@ tft_status tft_polymul_batch(tft_ctx* ctx, const tft_polymul_desc* descs,
                              void* stream);
 
 /*
+ * Device operand generator (not part of the paper's method: it lets a
+ * served request carry only its identifier and lengths).  Writes n residues
+ * of operand `operand` (0 = a, 1 = b) of request `request` under `seed` to
+ * the device buffer out (16-byte aligned, n elements of the context's
+ * prime): element i is v mod p for the 128-bit output
+ * v = x0 + 2^32 x1 + 2^64 x2 + 2^96 x3 of Philox4x32-10 (Salmon, Moraes,
+ * Dror, Shaw, SC 2011) with counter (i, operand, request mod 2^32,
+ * request div 2^32) and key (seed mod 2^32, seed div 2^32).  Asynchronous
+ * on `stream`.  Errors: TFT_EINVAL (null or misaligned out, n = 0,
+ * operand > 1).
+ */
+tft_status tft_generate(tft_ctx* ctx, uint64_t seed, uint64_t request,
+                        uint32_t operand, void* out, uint64_t n, void* stream);
+
+/*
+ * Device bytes one served request occupies while in flight (its in-place
+ * footprint, the unit of the server's admission budget): a (na), b (nb) and
+ * the product (na + nb - 1 elements), plus the row/column class's work area
+ * (B' and two rows, as tft_batch_work_words), each part rounded up to 256
+ * bytes.  Host only.
+ */
+tft_status tft_request_bytes(tft_prime prime, uint64_t na, uint64_t nb,
+                             const tft_batch_params* params, uint64_t* bytes);
+
+/*
+ * Arena: the server's device-memory bookkeeping, exposed so that its
+ * policy can be checked without a device.  First-fit allocation of byte
+ * ranges of [0, size) in multiples of `align` (a power of two), free ranges
+ * merged on release.  Host only; offsets, not pointers.
+ * tft_arena_alloc returns TFT_ENOMEM when no free range is large enough;
+ * tft_arena_free takes an offset returned by tft_arena_alloc (TFT_EINVAL
+ * otherwise).  tft_arena_usage: bytes in use, the peak since creation, and
+ * the number of free ranges.
+ */
+typedef struct tft_arena tft_arena;
+tft_status tft_arena_create(uint64_t size, uint64_t align, tft_arena** out);
+tft_status tft_arena_destroy(tft_arena* arena);
+tft_status tft_arena_alloc(tft_arena* arena, uint64_t bytes,
+                           uint64_t* offset);
+tft_status tft_arena_free(tft_arena* arena, uint64_t offset);
+tft_status tft_arena_usage(tft_arena* arena, uint64_t* used, uint64_t* peak,
+                           uint64_t* free_ranges);
+
+/*
+ * Served products: a stream of requests, each the product of two operands
+ * produced by tft_generate, answered through the batched product with
+ * continuous batching.
+ *
+ * tft_server_create reserves budget_bytes of device memory (the admission
+ * budget), its own stream and two descriptor tables of max_batch products
+ * (two batches in flight).  The server borrows ctx (which must outlive it)
+ * for the roots, the launch counting and, in one-by-one mode, the
+ * single-call product; the batched mode uses `params` as its schedule.
+ *
+ * tft_server_replay runs `count` requests open loop: request i becomes
+ * available reqs[i].arrival_s seconds after the start (arrival times
+ * non-decreasing).  Mode TFT_SERVE_BATCHED: whenever one of the two batch
+ * slots is free, every available request is admitted in arrival order while
+ * its tft_request_bytes fit in the budget (at most max_batch per batch), and
+ * the admitted requests' operands are generated and multiplied as one
+ * batch; a request's memory is released when its batch completes.  Mode
+ * TFT_SERVE_ONE_BY_ONE: each request, as it arrives, is generated and
+ * multiplied by itself with tft_polymul on the server's stream (the plain
+ * path, for comparison).  done_s[i] (optional) receives the completion time
+ * of request i in seconds from the start, measured by CUDA events; where
+ * keep[i] is non-null (optional array), the product of request i (na + nb
+ * - 1 elements) is copied there before its memory is released.  The call
+ * returns when every request has completed; stats (optional) summarise the
+ * run.  Errors: TFT_EINVAL (bad request, unsorted arrivals, misaligned
+ * keep), TFT_ERANGE (a request larger than the budget, or, one by one,
+ * longer than the context's max_len), TFT_ECUDA.
+ */
+typedef struct tft_server tft_server;
+typedef struct tft_request {
+  uint64_t id;        /* generator counter of the operands */
+  uint64_t na;
+  uint64_t nb;
+  double arrival_s;   /* scheduled arrival, seconds from the start */
+} tft_request;
+typedef struct tft_server_stats {
+  uint64_t completed;
+  uint64_t batches;     /* batches launched (one by one: requests) */
+  uint64_t max_batch;   /* most requests in one batch */
+  uint64_t peak_bytes;  /* most budget bytes in use at once */
+  uint64_t launches;    /* kernels launched */
+  double wall_s;        /* host time from the start to the last completion */
+} tft_server_stats;
+#define TFT_SERVE_BATCHED 0
+#define TFT_SERVE_ONE_BY_ONE 1
+tft_status tft_server_create(tft_ctx* ctx, uint64_t budget_bytes,
+                             uint32_t max_batch,
+                             const tft_batch_params* params,
+                             tft_server** out);
+tft_status tft_server_destroy(tft_server* server);
+tft_status tft_server_replay(tft_server* server, const tft_request* reqs,
+                             uint64_t count, uint64_t seed, int mode,
+                             double* done_s, void* const* keep,
+                             tft_server_stats* stats);
+
+/*
  * tft_forward_noalloc: the in-place forward TFT of tft_forward, for callers
  * that must not allocate device memory and so cannot create a context --
  * for example a serving loop whose device memory is fully reserved at
@@ -283,7 +383,7 @@ const char* tft_last_cuda_error(void);
  * spent waiting for an SM.  Profiling must be off while a stream is being captured
  * into a CUDA graph.
  */
-#define TFT_NUM_KERNEL_KINDS 10
+#define TFT_NUM_KERNEL_KINDS 11
 tft_status tft_profile_enable(tft_ctx* ctx, int enable);
 tft_status tft_profile_read(tft_ctx* ctx, double* ms, uint64_t* launches);
 const char* tft_kernel_name(int kind);

@@ -1,4 +1,5 @@
-"""ctypes wrapper around the plain-C oracle ``oracle/alg_c.c``.
+"""ctypes wrapper around the plain-C oracle (``oracle/alg_c.c`` and the
+served workload's generator ``oracle/gen_c.c``).
 
 Test infrastructure only.  ``build()`` compiles the C file with gcc -O2 into
 ``oracle/_build/liborc.so`` (git-ignored); every function takes and returns
@@ -17,6 +18,7 @@ from . import field as _f
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "alg_c.c")
+_SRCS = [_SRC, os.path.join(_HERE, "gen_c.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_OUT_DIR, "liborc.so")
 _lib = None
@@ -28,11 +30,11 @@ def build(force=False):
     """Compile the C oracle (gcc -O2, no architecture-specific flags)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if not force and os.path.exists(_LIB) and \
-            os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS):
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
-                           "-o", tmp, _SRC])
+                           "-o", tmp] + _SRCS)
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -65,6 +67,14 @@ def lib():
         L.orc_eval_tft_points.restype = ctypes.c_int
         L.orc_eval_tft_points.argtypes = [ctypes.c_int, _u64p, ctypes.c_uint64,
                                           _u64p, ctypes.c_uint64, _u64p]
+        L.orc_philox4x32_10.restype = None
+        L.orc_philox4x32_10.argtypes = [ctypes.POINTER(ctypes.c_uint32),
+                                        ctypes.POINTER(ctypes.c_uint32),
+                                        ctypes.POINTER(ctypes.c_uint32)]
+        L.orc_gen_operand.restype = ctypes.c_int
+        L.orc_gen_operand.argtypes = [ctypes.c_int, ctypes.c_uint64,
+                                      ctypes.c_uint64, ctypes.c_uint32,
+                                      ctypes.c_uint64, _u64p]
         _lib = L
     return _lib
 
@@ -161,3 +171,25 @@ def omega(prime, s):
 
 def omega_k(prime, k):
     return int(lib().orc_omega_k(_pid(prime), int(k)))
+
+
+def philox4x32_10(counter, key):
+    """The four output words of Philox4x32-10 for a 4-word counter and a
+    2-word key (the generator's definition, in plain C)."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in counter])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return tuple(int(v) for v in o)
+
+
+def gen_operand(prime, seed, request, operand, n):
+    """Operand `operand` (0 = a, 1 = b) of served request `request`: n
+    residues, element i = (Philox4x32-10 output as a 128-bit integer) mod p
+    with counter (i, operand, request lo, request hi), key (seed lo, hi)."""
+    out = np.zeros(int(n), dtype=np.uint64)
+    rc = lib().orc_gen_operand(_pid(prime), int(seed), int(request),
+                               int(operand), int(n), _ptr(out))
+    if rc:
+        raise ValueError("orc_gen_operand failed")
+    return out

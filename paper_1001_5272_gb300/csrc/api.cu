@@ -8,74 +8,12 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/tft.h"
-#include "batch.cuh"
+#include "ctx.h"
 #include "field.cuh"
-#include "tft_internal.h"
 
 using namespace tftgb;
 
-namespace {
-
-typedef unsigned __int128 u128;
-
-struct PrimeInfo {
-  uint64_t p;
-  int K;
-  uint64_t g;
-  uint32_t w;  // element bytes
-};
-
-const PrimeInfo kPrimes[3] = {
-    {998244353ull, 23, 3, 4},
-    {2013265921ull, 27, 31, 4},
-    {0xFFFFFFFF00000001ull, 32, 7, 8},
-};
-
-uint64_t mulm(uint64_t a, uint64_t b, uint64_t p) {
-  return (uint64_t)(((u128)a * b) % p);
-}
-uint64_t powm(uint64_t a, uint64_t e, uint64_t p) {
-  uint64_t r = 1 % p;
-  a %= p;
-  while (e) {
-    if (e & 1) r = mulm(r, a, p);
-    a = mulm(a, a, p);
-    e >>= 1;
-  }
-  return r;
-}
-uint64_t rev_bits(uint64_t s, int k) {
-  uint64_t o = 0;
-  for (int i = 0; i < k; i++) {
-    o = (o << 1) | (s & 1);
-    s >>= 1;
-  }
-  return o;
-}
-// omega_s = omega_[K]^(rev_K s)
-uint64_t omega_s(const PrimeInfo& pr, uint64_t s) {
-  uint64_t top = powm(pr.g, (pr.p - 1) >> pr.K, pr.p);
-  return powm(top, rev_bits(s, pr.K), pr.p);
-}
-// twiddle form: Montgomery (x 2^32) for the 32-bit primes, identity otherwise
-uint64_t to_tw(const PrimeInfo& pr, uint64_t x) {
-  if (pr.w == 8) return x % pr.p;
-  return (uint64_t)((((u128)(x % pr.p)) << 32) % pr.p);
-}
-
-int ceil_log2(uint64_t n) {
-  int l = 0;
-  while ((1ull << l) < n) ++l;
-  return l;
-}
-
-bool valid_prime(int prime) { return prime >= 0 && prime < 3; }
-
-// Largest transform length the two-pass plan handles.
-uint64_t max_supported(const PrimeInfo& pr) {
-  return pr.w == 8 ? (1ull << 25) : (1ull << 27);
-}
+namespace tftgb {
 
 // Choose the plan for length n (see tft_internal.h).  Returns false if n is
 // beyond the supported range.
@@ -130,72 +68,9 @@ bool make_plan(int prime, uint64_t n, Plan* out) {
   return true;
 }
 
-// RAII switch to the context's device.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) {
-      ok = false;
-      return;
-    }
-    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev)
-      cudaSetDevice(prev);
-  }
-};
 
-bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+}  // namespace tftgb
 
-bool overlap(const void* a, uint64_t abytes, const void* b, uint64_t bbytes) {
-  const uintptr_t a0 = (uintptr_t)a, a1 = a0 + abytes;
-  const uintptr_t b0 = (uintptr_t)b, b1 = b0 + bbytes;
-  return a0 < b1 && b0 < a1;
-}
-
-}  // namespace
-
-constexpr int kProfSlots = 64;
-
-struct ProfSlot {
-  cudaEvent_t start;
-  cudaEvent_t stop;
-  int kind;
-};
-
-struct tft_ctx {
-  int prime;
-  int device;
-  int nsm;
-  uint64_t max_len;
-  uint32_t flags;
-  PrimeInfo pr;
-  alignas(16) unsigned char rt[sizeof(RootTable<uint64_t>)];
-  void* scratch;     // 3 * 2^14 words: E / EA, EB
-  void* work;        // max_len words (products)
-  void* stage;       // 3 * max_len words (host-buffer entry points)
-  tft_status sticky;
-  // launch accounting and optional per-kernel timing
-  uint64_t launches;
-  int prof_on;
-  int prof_pending;
-  ProfSlot prof[kProfSlots];
-  double prof_ms[K_NUM_KINDS];
-  uint64_t prof_count[K_NUM_KINDS];
-  LaunchHook hook;
-  AuxStreams aux;    // side stream + fork/join events
-  // batched products (tft_ctx_reserve_batch / tft_batch_plan)
-  void* batch_tab;         // device descriptor tables
-  uint64_t batch_tab_bytes;
-  void* batch_work;        // work area of the large products
-  uint64_t batch_work_words;
-  uint32_t batch_max;      // products per plan
-  BatchLaunch batch;       // the current plan
-  int batch_ready;
-};
 
 namespace {
 
@@ -286,10 +161,26 @@ bool g_prepared[3][64] = {};
 
 thread_local const char* g_last_cuda_error = "no error";
 
+}  // namespace
+
+namespace tftgb {
+
 cudaError_t note(cudaError_t e) {
   if (e != cudaSuccess) g_last_cuda_error = cudaGetErrorName(e);
   return e;
 }
+
+tft_status from_cuda(tft_ctx* ctx, cudaError_t e) {
+  if (e == cudaSuccess) return TFT_OK;
+  note(e);
+  if (ctx) ctx->sticky = TFT_ECUDA;
+  return TFT_ECUDA;
+}
+
+}  // namespace tftgb
+
+namespace {
+
 
 void prof_drain(tft_ctx* c) {
   for (int i = 0; i < c->prof_pending; ++i) {
@@ -333,12 +224,6 @@ tft_status check_transform_args(tft_ctx* ctx, const void* x, uint64_t n,
   return TFT_OK;
 }
 
-tft_status from_cuda(tft_ctx* ctx, cudaError_t e) {
-  if (e == cudaSuccess) return TFT_OK;
-  note(e);
-  if (ctx) ctx->sticky = TFT_ECUDA;
-  return TFT_ECUDA;
-}
 
 // One staging slot: max_len words rounded up to 256 bytes.
 size_t stage_slot_bytes(const tft_ctx* ctx) {
@@ -644,231 +529,6 @@ tft_status tft_polymul_host(tft_ctx* ctx, const void* a_host, uint64_t na,
   return from_cuda(ctx, cudaStreamSynchronize(s));
 }
 
-// ---------------------------------------------------------------------------
-// Batched products
-// ---------------------------------------------------------------------------
-namespace {
-
-struct BatchDefaults {
-  int small_log, lr, clog;
-};
-
-BatchDefaults batch_defaults(const PrimeInfo& pr) {
-  // small class in one CTA up to 2^13 words (u32) / 2^12 (u64); the large
-  // class on rows of 2^9 (u32) / 2^10 (u64) with 16 / 4 columns per tile
-  if (pr.w == 8) return {12, 10, 2};
-  return {13, 9, 4};
-}
-
-}  // namespace
-
-tft_status tft_ctx_reserve_batch(tft_ctx* ctx, uint32_t max_products,
-                                 uint64_t work_words) {
-  if (!ctx || max_products == 0) return TFT_EINVAL;
-  DeviceGuard g(ctx->device);
-  if (!g.ok) return TFT_ECUDA;
-  if (ctx->batch_tab) cudaFree(ctx->batch_tab);
-  if (ctx->batch_work) cudaFree(ctx->batch_work);
-  ctx->batch_tab = ctx->batch_work = nullptr;
-  ctx->batch_ready = 0;
-  ctx->batch_tab_bytes =
-      (uint64_t)max_products * (sizeof(BatchLarge) + sizeof(BatchSmall));
-  if (cudaMalloc(&ctx->batch_tab, ctx->batch_tab_bytes) != cudaSuccess) {
-    ctx->batch_tab = nullptr;
-    return TFT_ENOMEM;
-  }
-  ctx->batch_work_words = work_words;
-  if (work_words &&
-      cudaMalloc(&ctx->batch_work, work_words * ctx->pr.w) != cudaSuccess) {
-    cudaFree(ctx->batch_tab);
-    ctx->batch_tab = ctx->batch_work = nullptr;
-    return TFT_ENOMEM;
-  }
-  ctx->batch_max = max_products;
-  return TFT_OK;
-}
-
-tft_status tft_batch_plan(tft_ctx* ctx, const tft_polymul_desc* descs,
-                          uint32_t count, const tft_batch_params* params) {
-  if (!ctx || (!descs && count)) return TFT_EINVAL;
-  if (!ctx->batch_tab) return TFT_EINVAL;
-  if (count > ctx->batch_max) return TFT_ERANGE;
-  ctx->batch_ready = 0;
-  const PrimeInfo& pr = ctx->pr;
-  const size_t w = pr.w;
-  BatchDefaults P = batch_defaults(pr);
-  if (params) {
-    if (params->small_log) P.small_log = (int)params->small_log;
-    if (params->lr) P.lr = (int)params->lr;
-    if (params->clog_plus1) P.clog = (int)params->clog_plus1 - 1;
-  }
-  const int small_max = pr.w == 8 ? 12 : 13;
-  const int c_max = pr.w == 8 ? 12 : 13;
-  if (P.lr < 8 || P.lr > 12 || P.small_log < P.lr ||
-      P.small_log > small_max || P.clog < 0 || P.clog > 4 ||
-      P.clog > P.lr)
-    return TFT_EINVAL;
-  const uint64_t R = 1ull << P.lr;
-  const uint32_t C = 1u << P.clog;
-  std::vector<BatchSmall> hs;
-  std::vector<BatchLarge> hl;
-  hs.reserve(count);
-  hl.reserve(count);
-  uint64_t work_off = 0;  // words
-  int lmax = 0, cmax = 0;
-  for (uint32_t i = 0; i < count; ++i) {
-    const tft_polymul_desc& d = descs[i];
-    if (!d.a || !d.b || !d.out || d.na == 0 || d.nb == 0) return TFT_EINVAL;
-    if (!aligned16(d.a) || !aligned16(d.b) || !aligned16(d.out))
-      return TFT_EINVAL;
-    const uint64_t r = d.na + d.nb - 1;
-    if (overlap(d.out, r * w, d.a, d.na * w) ||
-        overlap(d.out, r * w, d.b, d.nb * w))
-      return TFT_EINVAL;
-    if (r <= (1ull << P.small_log)) {
-      BatchSmall q;
-      q.a = (uint64_t)d.a;
-      q.b = (uint64_t)d.b;
-      q.out = (uint64_t)d.out;
-      q.na = (uint32_t)d.na;
-      q.nb = (uint32_t)d.nb;
-      q.l = (uint32_t)ceil_log2(r);
-      q.pad = 0;
-      lmax = std::max(lmax, (int)q.l);
-      hs.push_back(q);
-      continue;
-    }
-    BatchLarge q;
-    memset(&q, 0, sizeof(q));
-    q.A = (uint32_t)(r >> P.lr);
-    q.Bm = (uint32_t)(r & (R - 1));
-    const uint64_t rows = q.A + (q.Bm ? 1 : 0);
-    if (rows > (1ull << c_max)) return TFT_ERANGE;
-    q.c = (uint32_t)ceil_log2(rows);
-    cmax = std::max(cmax, (int)q.c);
-    q.a = (uint64_t)d.a;
-    q.b = (uint64_t)d.b;
-    q.out = (uint64_t)d.out;
-    q.na = d.na;
-    q.nb = d.nb;
-    q.omega_a_tw = to_tw(pr, omega_s(pr, q.A));
-    // work area: B' (r words) then EA and EB (R words each), 16-byte slots
-    const uint64_t align = 16 / w;
-    auto take = [&](uint64_t words) {
-      const uint64_t at = work_off;
-      work_off += (words + align - 1) / align * align;
-      return at;
-    };
-    const uint64_t wo = take(r), ea = take(R), eb = take(R);
-    q.work = wo;  // offsets for now, pointers below
-    q.EA = ea;
-    q.EB = eb;
-    hl.push_back(q);
-  }
-  if (work_off > ctx->batch_work_words) return TFT_ERANGE;
-  // the column tile of the longest large product must fit in shared memory
-  // next to the kernel's static copy of the root table
-  if (!hl.empty()) {
-    int optin = 0;
-    DeviceGuard g0(ctx->device);
-    if (!g0.ok || cudaDeviceGetAttribute(&optin,
-                                         cudaDevAttrMaxSharedMemoryPerBlockOptin,
-                                         ctx->device) != cudaSuccess)
-      return from_cuda(ctx, cudaErrorUnknown);
-    const size_t need =
-        w == 8 ? col_smem_bytes<uint64_t>(cmax, P.clog)
-               : col_smem_bytes<uint32_t>(cmax, P.clog);
-    if (need + sizeof(RootTable<uint64_t>) + 256 > (size_t)optin)
-      return TFT_ERANGE;
-  }
-  // small products largest first (the persistent CTAs then balance better)
-  std::sort(hs.begin(), hs.end(), [](const BatchSmall& x, const BatchSmall& y) {
-    return x.na + x.nb > y.na + y.nb;
-  });
-  uint64_t rows_acc = 0, cs_acc = 0, cl_acc = 0;
-  unsigned char* wbase = (unsigned char*)ctx->batch_work;
-  for (BatchLarge& q : hl) {
-    q.work = (uint64_t)(wbase + q.work * w);
-    q.EA = (uint64_t)(wbase + q.EA * w);
-    q.EB = (uint64_t)(wbase + q.EB * w);
-    q.row_base = rows_acc;
-    q.cs_base = cs_acc;
-    q.cl_base = cl_acc;
-    rows_acc += q.A;
-    cs_acc += (R - q.Bm + C - 1) / C;
-    cl_acc += (q.Bm + C - 1) / C;
-  }
-  DeviceGuard g(ctx->device);
-  if (!g.ok) return TFT_ECUDA;
-  unsigned char* tab = (unsigned char*)ctx->batch_tab;
-  const size_t lbytes = hl.size() * sizeof(BatchLarge);
-  const size_t sbytes = hs.size() * sizeof(BatchSmall);
-  if (lbytes && cudaMemcpy(tab, hl.data(), lbytes, cudaMemcpyHostToDevice) !=
-                    cudaSuccess)
-    return from_cuda(ctx, cudaErrorUnknown);
-  const size_t soff = (lbytes + 255) & ~(size_t)255;
-  if (sbytes && cudaMemcpy(tab + soff, hs.data(), sbytes,
-                           cudaMemcpyHostToDevice) != cudaSuccess)
-    return from_cuda(ctx, cudaErrorUnknown);
-  BatchLaunch& B = ctx->batch;
-  B.large = tab;
-  B.nl = (uint32_t)hl.size();
-  B.small = tab + soff;
-  B.ns = (uint32_t)hs.size();
-  B.lmax = lmax;
-  B.lr = P.lr;
-  B.clog = P.clog;
-  B.cmax = cmax;
-  B.total_rows = rows_acc;
-  B.cs_tiles = cs_acc;
-  B.cl_tiles = cl_acc;
-  ctx->batch_ready = 1;
-  return TFT_OK;
-}
-
-tft_status tft_batch_run(tft_ctx* ctx, void* stream) {
-  if (!ctx) return TFT_EINVAL;
-  if (!ctx->batch_ready) return TFT_EINVAL;
-  DeviceGuard g(ctx->device);
-  if (!g.ok) return TFT_ECUDA;
-  return from_cuda(ctx, launch_batch(ctx->prime, ctx->batch, ctx->rt,
-                                     ctx->nsm, (cudaStream_t)stream,
-                                     &ctx->hook, &ctx->aux));
-}
-
-tft_status tft_polymul_batch(tft_ctx* ctx, const tft_polymul_desc* descs,
-                             uint32_t count, const tft_batch_params* params,
-                             void* stream) {
-  tft_status st = tft_batch_plan(ctx, descs, count, params);
-  if (st != TFT_OK) return st;
-  return tft_batch_run(ctx, stream);
-}
-
-tft_status tft_batch_work_words(tft_prime prime, const tft_polymul_desc* descs,
-                                uint32_t count, const tft_batch_params* params,
-                                uint64_t* words) {
-  if (!valid_prime((int)prime) || (!descs && count) || !words)
-    return TFT_EINVAL;
-  const PrimeInfo& pr = kPrimes[(int)prime];
-  BatchDefaults P = batch_defaults(pr);
-  if (params) {
-    if (params->small_log) P.small_log = (int)params->small_log;
-    if (params->lr) P.lr = (int)params->lr;
-  }
-  const uint64_t R = 1ull << P.lr;
-  const uint64_t align = 16 / pr.w;
-  uint64_t total = 0;
-  for (uint32_t i = 0; i < count; ++i) {
-    const uint64_t r = descs[i].na + descs[i].nb - 1;
-    if (descs[i].na == 0 || descs[i].nb == 0) return TFT_EINVAL;
-    if (r <= (1ull << P.small_log)) continue;
-    total += (r + align - 1) / align * align + 2 * ((R + align - 1) / align * align);
-  }
-  *words = total;
-  return TFT_OK;
-}
-
-
 tft_status tft_footprint(tft_prime prime, uint64_t n, uint32_t k, int op,
                          uint64_t* inplace_bytes, uint64_t* padded_bytes) {
   if (!valid_prime((int)prime) || !inplace_bytes || !padded_bytes || n == 0)
@@ -946,7 +606,7 @@ const char* tft_kernel_name(int kind) {
   static const char* names[K_NUM_KINDS] = {
       "k_small",   "k_small_mul",   "k_col_fwd",     "k_row_fwd",
       "k_row_inv", "k_col_inv",     "k_lastrow_inv", "k_row_mul",
-      "k_lastrow_fwd", "k_lastrow_mul"};
+      "k_lastrow_fwd", "k_lastrow_mul", "k_gen"};
   return (kind >= 0 && kind < K_NUM_KINDS) ? names[kind] : "unknown";
 }
 

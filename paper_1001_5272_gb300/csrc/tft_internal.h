@@ -19,7 +19,8 @@ enum KernelKind {
   K_ROW_MUL = 7,
   K_LASTROW_FWD = 8,   // ragged last row of a forward transform
   K_LASTROW_MUL = 9,   // ragged last row of a product (forward + pointwise)
-  K_NUM_KINDS = 10
+  K_GEN = 10,          // served-request operand generator
+  K_NUM_KINDS = 11
 };
 
 // Called around every kernel launch (may be null).
@@ -80,6 +81,24 @@ struct BatchLaunch {
 cudaError_t launch_batch(int prime, const BatchLaunch& B, const void* rt,
                          int nsm, cudaStream_t s, const LaunchHook* hook,
                          const AuxStreams* aux);
+
+// Operand generator of served requests (gen.cu): one descriptor per
+// (request, operand); chunk_base is the prefix of gen_chunks(n).
+struct GenDesc {
+  uint64_t dst;         // device pointer
+  uint64_t n;           // elements
+  uint64_t request;
+  uint64_t chunk_base;
+  uint32_t operand;     // 0 = a, 1 = b
+  uint32_t pad;
+};
+uint64_t gen_chunks(uint64_t n);
+cudaError_t launch_gen_table(int prime, const GenDesc* d, uint32_t nd,
+                             uint64_t chunks, uint64_t seed, int nsm,
+                             cudaStream_t s);
+cudaError_t launch_gen_pair(int prime, void* a, uint64_t na, void* b,
+                            uint64_t nb, uint64_t request, uint64_t seed,
+                            int nsm, cudaStream_t s);
 
 cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
                            void* E, const void* rt, int nsm, cudaStream_t s,

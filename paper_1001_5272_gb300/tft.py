@@ -42,6 +42,24 @@ class BatchParams(ctypes.Structure):
                 ("clog_plus1", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class Request(ctypes.Structure):
+    """tft_request: one served request."""
+    _fields_ = [("id", ctypes.c_uint64), ("na", ctypes.c_uint64),
+                ("nb", ctypes.c_uint64), ("arrival_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    """tft_server_stats."""
+    _fields_ = [("completed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("max_batch", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("wall_s", ctypes.c_double)]
+
+
+TFT_SERVE_BATCHED = 0
+TFT_SERVE_ONE_BY_ONE = 1
+
+
 class TFTError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -93,6 +111,22 @@ def load():
         "tft_batch_run": (i32, [vp, vp]),
         "tft_polymul_batch": (i32, [vp, ctypes.POINTER(PolymulDesc), u32,
                                     ctypes.POINTER(BatchParams), vp]),
+        "tft_generate": (i32, [vp, u64, u64, u32, vp, u64, vp]),
+        "tft_request_bytes": (i32, [i32, u64, u64, ctypes.POINTER(BatchParams),
+                                    ctypes.POINTER(u64)]),
+        "tft_arena_create": (i32, [u64, u64, ctypes.POINTER(vp)]),
+        "tft_arena_destroy": (i32, [vp]),
+        "tft_arena_alloc": (i32, [vp, u64, ctypes.POINTER(u64)]),
+        "tft_arena_free": (i32, [vp, u64]),
+        "tft_arena_usage": (i32, [vp, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                  ctypes.POINTER(u64)]),
+        "tft_server_create": (i32, [vp, u64, u32, ctypes.POINTER(BatchParams),
+                                    ctypes.POINTER(vp)]),
+        "tft_server_destroy": (i32, [vp]),
+        "tft_server_replay": (i32, [vp, ctypes.POINTER(Request), u64, u64, i32,
+                                    ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(vp),
+                                    ctypes.POINTER(ServerStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -292,7 +326,7 @@ def tft_last_error(ctx):
     return int(load().tft_last_error(ctx.handle))
 
 
-NUM_KERNEL_KINDS = 10
+NUM_KERNEL_KINDS = 11
 
 
 def kernel_name(kind):
@@ -404,3 +438,124 @@ def tft_polymul_batch(ctx, products, params=None, stream=None):
                                     len(products), _params(params),
                                     _stream_handle(stream)),
            "tft_polymul_batch")
+
+
+# ---------------------------------------------------------------------------
+# Served products
+# ---------------------------------------------------------------------------
+
+def tft_generate(ctx, seed, request, operand, out, stream=None):
+    """Fill the CUDA tensor ``out`` with operand ``operand`` of request
+    ``request`` (device generator, Philox4x32-10 reduced mod p)."""
+    _check(load().tft_generate(ctx.handle, int(seed), int(request),
+                               int(operand),
+                               _dev_ptr(out, ctx.elem_bytes, "out"),
+                               out.numel(), _stream_handle(stream)),
+           "tft_generate")
+
+
+def tft_request_bytes(prime, na, nb, params=None):
+    v = ctypes.c_uint64()
+    _check(load().tft_request_bytes(prime_id(prime), int(na), int(nb),
+                                    _params(params), ctypes.byref(v)),
+           "tft_request_bytes")
+    return v.value
+
+
+class Arena:
+    """The server's first-fit arena (host bookkeeping of offsets)."""
+
+    def __init__(self, size, align=256):
+        h = ctypes.c_void_p()
+        _check(load().tft_arena_create(int(size), int(align),
+                                       ctypes.byref(h)), "tft_arena_create")
+        self._h = h
+
+    def alloc(self, nbytes):
+        """Offset of a new range, or None when nothing fits."""
+        off = ctypes.c_uint64()
+        st = load().tft_arena_alloc(self._h, int(nbytes), ctypes.byref(off))
+        if st == TFT_ENOMEM:
+            return None
+        _check(st, "tft_arena_alloc")
+        return off.value
+
+    def free(self, offset):
+        _check(load().tft_arena_free(self._h, int(offset)), "tft_arena_free")
+
+    def usage(self):
+        u, p, f = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().tft_arena_usage(self._h, ctypes.byref(u),
+                                      ctypes.byref(p), ctypes.byref(f)),
+               "tft_arena_usage")
+        return {"used": u.value, "peak": p.value, "free_ranges": f.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().tft_arena_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """tft_server: continuous batching of generated requests under a device
+    memory budget (or the one-by-one comparison path)."""
+
+    def __init__(self, ctx, budget_bytes, max_batch=4096, params=None):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(load().tft_server_create(ctx.handle, int(budget_bytes),
+                                        int(max_batch), _params(params),
+                                        ctypes.byref(h)), "tft_server_create")
+        self._h = h
+
+    def replay(self, ids, na, nb, arrivals, seed, mode="batched", keep=None):
+        """Run the requests open loop; returns (completion seconds as a
+        numpy array, stats dict).  keep: optional {index: CUDA tensor of
+        na + nb - 1 elements} receiving those requests' products."""
+        import numpy as np
+        n = len(ids)
+        reqs = (Request * max(1, n))()
+        for i in range(n):
+            reqs[i].id = int(ids[i])
+            reqs[i].na = int(na[i])
+            reqs[i].nb = int(nb[i])
+            reqs[i].arrival_s = float(arrivals[i])
+        done = np.zeros(max(1, n), dtype=np.float64)
+        keep_arr = None
+        if keep:
+            keep_arr = (ctypes.c_void_p * max(1, n))()
+            for i, t in keep.items():
+                if t.numel() != int(na[i]) + int(nb[i]) - 1:
+                    raise ValueError(f"keep[{i}] has the wrong length")
+                keep_arr[i] = _dev_ptr(t, self.ctx.elem_bytes, "keep").value
+        st = ServerStats()
+        m = TFT_SERVE_BATCHED if mode == "batched" else TFT_SERVE_ONE_BY_ONE
+        _check(load().tft_server_replay(
+            self._h, reqs, n, int(seed), m,
+            done.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+            keep_arr, ctypes.byref(st)), "tft_server_replay")
+        stats = {k: getattr(st, k) for k, _ in ServerStats._fields_}
+        return done[:n], stats
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().tft_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
