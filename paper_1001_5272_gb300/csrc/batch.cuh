@@ -91,7 +91,8 @@ k_small_mul_batch(const BatchSmall* __restrict__ d, uint32_t n, int lmax,
       Z[2 * i] = i < r ? F::mul_data(Z[2 * i], Z[2 * i + 1]) : T(0);
     __syncthreads();
     inv_block<F>(Z, 0, 1, l, r, tw);
-    for (uint32_t i = threadIdx.x; i < r; i += blockDim.x) out[i] = Z[2 * i];
+    for (uint32_t i = threadIdx.x; i < r; i += blockDim.x)
+      out[i] = F::canon(Z[2 * i]);
   }
 }
 
@@ -231,7 +232,8 @@ k_lastrow_inv_batch(const BatchLarge* __restrict__ d, uint32_t nl, int lr,
     __syncthreads();
     RowTw<F> tw{W, Wih, L, &s_rt, q.A, lr};
     inv_block<F>(Z, 0, 0, lr, q.Bm, tw);
-    for (uint32_t i = threadIdx.x; i < q.Bm; i += blockDim.x) row[i] = Z[i];
+    for (uint32_t i = threadIdx.x; i < q.Bm; i += blockDim.x)
+      row[i] = F::canon(Z[i]);
   }
 }
 

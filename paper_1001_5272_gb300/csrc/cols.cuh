@@ -91,11 +91,11 @@ __device__ __forceinline__ void col_fwd_stage(
       if (LAST) {
         if (colok && t < rows) {
           if (t < a)
-            dst[q + (uint64_t)t * R] = x[i];
+            dst[q + (uint64_t)t * R] = F::canon(x[i]);
           else if (q < b)
-            dst[q + a * R] = x[i];
+            dst[q + a * R] = F::canon(x[i]);
           else
-            E[q] = x[i];
+            E[q] = F::canon(x[i]);
         }
       } else {
         Z[(tswz(t, clog) << clog) + cc] = x[i];
@@ -402,7 +402,8 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
   for (uint32_t i = threadIdx.x; i < (m << clog); i += blockDim.x) {
     const uint32_t t = i >> clog, cc = i & (C - 1);
     const uint64_t q = (uint64_t)q0 + cc;
-    if (q < q_end) X[q + (uint64_t)t * R] = Z[(tswz(t, clog) << clog) + cc];
+    if (q < q_end)
+      X[q + (uint64_t)t * R] = F::canon(Z[(tswz(t, clog) << clog) + cc]);
   }
   if (want_E) {
     const uint32_t tpc = blockDim.x >> clog;  // threads per column
@@ -434,7 +435,7 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
       for (uint32_t k2 = 0; k2 < tpc; ++k2)
         sacc = F::add(sacc, part[(k2 << clog) + threadIdx.x]);
       const uint64_t q = (uint64_t)q0 + threadIdx.x;
-      if (q < q_end) E[q] = sacc;
+      if (q < q_end) E[q] = F::canon(sacc);
     }
   }
 }

@@ -7,13 +7,14 @@
 //   p = 2013265921       =  15 * 2^27 + 1   (uint32 storage, Montgomery form)
 //   p = 2^64 - 2^32 + 1                      (uint64 storage, direct reduction)
 //
-// Data elements are always canonical residues in [0, p).  Twiddles are kept
-// in a per-field "twiddle form" that makes mul_tw(x, w) return x * w mod p in
-// canonical form:
+// Data elements in global memory are always canonical residues in [0, p)
+// (inside a transform the 64-bit field keeps values in [0, 2^64), see
+// Goldilocks; F::canon is applied at every store).  Twiddles are kept
+// in a per-field "twiddle form" that makes mul_tw(x, w) return x * w mod p:
 //   * 32-bit primes: w~ = w * 2^32 mod p and mul_tw is one Montgomery REDC of
-//     the 64-bit product (x * w~ * 2^-32 = x * w);
+//     the 64-bit product (x * w~ * 2^-32 = x * w), canonical;
 //   * 2^64 - 2^32 + 1: w~ = w and mul_tw reduces the 128-bit product using
-//     2^64 = 2^32 - 1 and 2^96 = -1 (mod p).
+//     2^64 = 2^32 - 1 and 2^96 = -1 (mod p), into [0, 2^64).
 #pragma once
 #include <stdint.h>
 
@@ -34,34 +35,84 @@ struct Goldilocks {
   static constexpr int K = 32;                     // two-adicity
   static constexpr int ID = 2;
 
-  static TFT_HD T add(T a, T b) {
-    T s = a + b;
-    // a carry out of 64 bits means the true sum is s + 2^64 = s + EPS (mod p)
-    // and then s + EPS < p; otherwise subtract p once if needed.
-    if (s < a) return s + EPS;
-    return s >= P ? s - P : s;
+  // Values inside a transform are kept in [0, 2^64) ("lazy": congruent to
+  // the residue, not necessarily below p); canon() maps them to [0, p) and
+  // every store to global memory goes through it.  The carry chains below
+  // use 2^64 = EPS (mod p): a carry out of bit 63 is worth EPS, a borrow
+  // costs EPS.
+
+  // a + b for any a, b < 2^64.  After one carry the wrapped sum is at most
+  // 2^64 - 2, and adding EPS can carry again only if it was >= p; the
+  // second wrapped value is then below 2^32, so a third carry cannot occur.
+  static __device__ __forceinline__ T add(T a, T b) {
+    uint32_t s0, s1, m;
+    asm("add.cc.u32 %0, %3, %5;\n\t"
+        "addc.cc.u32 %1, %4, %6;\n\t"
+        "addc.u32 %2, 0, 0;\n\t"
+        "sub.u32 %2, 0, %2;\n\t"
+        "add.cc.u32 %0, %0, %2;\n\t"
+        "addc.cc.u32 %1, %1, 0;\n\t"
+        "addc.u32 %2, 0, 0;\n\t"
+        "sub.u32 %2, 0, %2;\n\t"
+        "add.cc.u32 %0, %0, %2;\n\t"
+        "addc.u32 %1, %1, 0;"
+        : "=&r"(s0), "=&r"(s1), "=&r"(m)
+        : "r"((uint32_t)a), "r"((uint32_t)(a >> 32)), "r"((uint32_t)b),
+          "r"((uint32_t)(b >> 32)));
+    return ((uint64_t)s1 << 32) | s0;
   }
-  static TFT_HD T sub(T a, T b) {
-    T d = a - b;
-    return a < b ? d + P : d;  // wraps back into [0, p)
+  // a - b for any a, b < 2^64 (a borrow is repaid by subtracting EPS; a
+  // second borrow, possible only when b >= p, leaves a value near 2^64, so
+  // the second repayment cannot borrow).
+  static __device__ __forceinline__ T sub(T a, T b) {
+    uint32_t d0, d1, m;
+    asm("sub.cc.u32 %0, %3, %5;\n\t"
+        "subc.cc.u32 %1, %4, %6;\n\t"
+        "subc.u32 %2, 0, 0;\n\t"
+        "sub.cc.u32 %0, %0, %2;\n\t"
+        "subc.cc.u32 %1, %1, 0;\n\t"
+        "subc.u32 %2, 0, 0;\n\t"
+        "sub.cc.u32 %0, %0, %2;\n\t"
+        "subc.u32 %1, %1, 0;"
+        : "=&r"(d0), "=&r"(d1), "=&r"(m)
+        : "r"((uint32_t)a), "r"((uint32_t)(a >> 32)), "r"((uint32_t)b),
+          "r"((uint32_t)(b >> 32)));
+    return ((uint64_t)d1 << 32) | d0;
   }
-  // x = lo + 2^64 (hl + 2^32 hh)  ==  lo + (2^32 - 1) hl - hh  (mod p)
-  static TFT_HD T reduce128(uint64_t lo, uint64_t hi) {
-    const uint32_t hl = (uint32_t)hi;
-    const uint32_t hh = (uint32_t)(hi >> 32);
-    uint64_t t0 = lo - hh;
-    if (lo < hh) t0 -= EPS;                      // borrow: wrapped by +2^64
-    const uint64_t t1 = ((uint64_t)hl << 32) - hl;  // hl * (2^32 - 1)
-    uint64_t r = t0 + t1;
-    if (r < t1) r += EPS;                        // carry: wrapped by -2^64
-    return r >= P ? r - P : r;
+  // x = lo + 2^64 (hl + 2^32 hh)  ==  lo - hh + (2^32 - 1) hl  (mod p), for
+  // any 128-bit x; result in [0, 2^64).  t = lo - hh (a borrow costs EPS;
+  // t stays positive because lo - hh > -2^32), u = hl 2^32 - hl, then
+  // t + u with one carry worth EPS (t + u - 2^64 < 2^64 - 2^33, so adding
+  // EPS cannot carry).
+  static __device__ __forceinline__ T reduce128(uint64_t lo, uint64_t hi) {
+    uint32_t t0, t1, m, u0, u1;
+    asm("sub.cc.u32 %0, %5, %8;\n\t"
+        "subc.cc.u32 %1, %6, 0;\n\t"
+        "subc.u32 %2, 0, 0;\n\t"
+        "sub.cc.u32 %0, %0, %2;\n\t"
+        "subc.u32 %1, %1, 0;\n\t"
+        "sub.cc.u32 %3, 0, %7;\n\t"
+        "subc.u32 %4, %7, 0;\n\t"
+        "add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, 0, 0;\n\t"
+        "sub.u32 %2, 0, %2;\n\t"
+        "add.cc.u32 %0, %0, %2;\n\t"
+        "addc.u32 %1, %1, 0;"
+        : "=&r"(t0), "=&r"(t1), "=&r"(m), "=&r"(u0), "=&r"(u1)
+        : "r"((uint32_t)lo), "r"((uint32_t)(lo >> 32)), "r"((uint32_t)hi),
+          "r"((uint32_t)(hi >> 32)));
+    return ((uint64_t)t1 << 32) | t0;
   }
   static __device__ __forceinline__ T mul(T a, T b) {
     return reduce128(a * b, __umul64hi(a, b));
   }
   static __device__ __forceinline__ T mul_tw(T a, T w) { return mul(a, w); }
   static __device__ __forceinline__ T mul_data(T a, T b) { return mul(a, b); }
+  // a / 2 for any a < 2^64: (a - 1) / 2 + (p + 1) / 2 = (a + p) / 2 < 2^64
+  // when a is odd.
   static TFT_HD T half(T a) { return (a >> 1) + ((a & 1) ? HALF : 0); }
+  static TFT_HD T canon(T a) { return a >= P ? a - P : a; }
   static TFT_HD T one_tw() { return 1; }
 };
 
@@ -96,6 +147,7 @@ struct Mont32 {
     return redc((uint64_t)redc((uint64_t)a * b) * R2);
   }
   static TFT_HD T half(T a) { return (a + ((a & 1) ? P : 0)) >> 1; }
+  static TFT_HD T canon(T a) { return a; }  // always canonical
   static TFT_HD T one_tw() { return ONE; }
 };
 

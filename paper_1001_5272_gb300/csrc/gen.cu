@@ -49,7 +49,7 @@ template <>
 __device__ __forceinline__ uint64_t reduce_words<2>(uint4 x) {
   const uint64_t lo = (uint64_t)x.x | ((uint64_t)x.y << 32);
   const uint64_t hi = (uint64_t)x.z | ((uint64_t)x.w << 32);
-  return Goldilocks::reduce128(lo, hi);
+  return Goldilocks::canon(Goldilocks::reduce128(lo, hi));
 }
 
 template <uint64_t P>

@@ -80,7 +80,7 @@ k_small(typename F::T* __restrict__ x, uint32_t n, int l,
     fwd_pruned<F>(Z, 0, 0, l, n, tw);
   else
     inv_block<F>(Z, 0, 0, l, n, tw);
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = Z[i];
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = F::canon(Z[i]);
 }
 
 // Small TFT product: r = na + nb - 1 <= 2^l, both operands in one CTA.
@@ -112,7 +112,8 @@ k_small_mul(const typename F::T* __restrict__ a, uint32_t na,
     Z[2 * i] = i < r ? F::mul_data(Z[2 * i], Z[2 * i + 1]) : T(0);
   __syncthreads();
   inv_block<F>(Z, 0, 1, l, r, tw);
-  for (uint32_t i = threadIdx.x; i < r; i += blockDim.x) out[i] = Z[2 * i];
+  for (uint32_t i = threadIdx.x; i < r; i += blockDim.x)
+    out[i] = F::canon(Z[2 * i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -158,11 +159,11 @@ k_col_fwd(const typename F::T* src, uint64_t n_src, typename F::T* dst,
     const uint64_t q = q0 + (i & (C - 1));
     if (q >= q_end) continue;
     if (t < a)
-      dst[q + (uint64_t)t * R] = Z[i];
+      dst[q + (uint64_t)t * R] = F::canon(Z[i]);
     else if (q < b)
-      dst[q + a * R] = Z[i];
+      dst[q + a * R] = F::canon(Z[i]);
     else
-      E[q] = Z[i];
+      E[q] = F::canon(Z[i]);
   }
 }
 
@@ -198,7 +199,8 @@ k_row_fwd(typename F::T* X, const typename F::T* __restrict__ E, int lr,
     RowTw<F> tw{W, nullptr, L, &s_rt, rho, lr};
     const uint32_t nout = last ? (uint32_t)b : R;
     fwd_pruned<F>(Z, 0, 0, lr, nout, tw);
-    for (uint32_t q = threadIdx.x; q < nout; q += blockDim.x) row[q] = Z[q];
+    for (uint32_t q = threadIdx.x; q < nout; q += blockDim.x)
+      row[q] = F::canon(Z[q]);
     __syncthreads();
   }
 }
@@ -223,7 +225,8 @@ k_row_inv(typename F::T* X, int lr, uint64_t a, RootTable<typename F::T> rt) {
     __syncthreads();
     RowTw<F> tw{W, Wih, L, &s_rt, rho, lr};
     inv_full<F>(Z, 0, 0, lr, tw);
-    for (uint32_t q = threadIdx.x; q < R; q += blockDim.x) row[q] = Z[q];
+    for (uint32_t q = threadIdx.x; q < R; q += blockDim.x)
+      row[q] = F::canon(Z[q]);
     __syncthreads();
   }
 }
@@ -262,7 +265,7 @@ k_col_inv(typename F::T* X, typename F::T* __restrict__ E, int lr, uint32_t m,
   for (uint32_t i = threadIdx.x; i < (m << clog); i += blockDim.x) {
     const uint32_t t = i >> clog;
     const uint64_t q = q0 + (i & (C - 1));
-    if (q < q_end) X[q + (uint64_t)t * R] = Z[i];
+    if (q < q_end) X[q + (uint64_t)t * R] = F::canon(Z[i]);
   }
   if (want_E) {
     // threads per column: blockDim / C; each takes a contiguous chunk of rows
@@ -287,7 +290,7 @@ k_col_inv(typename F::T* X, typename F::T* __restrict__ E, int lr, uint32_t m,
       for (uint32_t kk = 0; kk < tpc; ++kk)
         s = F::add(s, part[(kk << clog) + threadIdx.x]);
       const uint64_t q = q0 + threadIdx.x;
-      if (q < q_end) E[q] = s;
+      if (q < q_end) E[q] = F::canon(s);
     }
   }
 }
@@ -315,7 +318,8 @@ k_lastrow_inv(typename F::T* X, const typename F::T* __restrict__ E, int lr,
   __syncthreads();
   RowTw<F> tw{W, Wih, L, &s_rt, a, lr};
   inv_block<F>(Z, 0, 0, lr, (uint32_t)b, tw);
-  for (uint32_t q = threadIdx.x; q < b; q += blockDim.x) row[q] = Z[q];
+  for (uint32_t q = threadIdx.x; q < b; q += blockDim.x)
+    row[q] = F::canon(Z[q]);
 }
 
 // ---------------------------------------------------------------------------
@@ -364,7 +368,7 @@ k_row_mul(typename F::T* out, const typename F::T* __restrict__ work,
     __syncthreads();
     if (!last) inv_full<F>(Z, 0, 1, lr, tw);
     for (uint32_t q = threadIdx.x; q < nout; q += blockDim.x)
-      orow[q] = Z[2 * q];
+      orow[q] = F::canon(Z[2 * q]);
     __syncthreads();
   }
 }

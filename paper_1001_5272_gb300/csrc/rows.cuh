@@ -176,7 +176,7 @@ __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
     for (int i = 0; i < U; ++i) {
       const uint32_t p = unit_pos(u, r_lo, L, i);
       if (DST_GLOBAL)
-        Grow[p] = x[i];
+        Grow[p] = F::canon(x[i]);
       else
         Zrow[swz(p)] = x[i];
     }
@@ -228,7 +228,7 @@ k_row_fwd2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
       __syncthreads();
     }
     if (active)
-      for (uint32_t q = t; q < R; q += Tpr) Grow[q] = Zrow[swz(q)];
+      for (uint32_t q = t; q < R; q += Tpr) Grow[q] = F::canon(Zrow[swz(q)]);
     __syncthreads();
   }
 }
@@ -453,7 +453,7 @@ __device__ __forceinline__ void row_last_body(
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i)
-      if (u * 16 + i < b) GA[u * 16 + i] = xa[i];
+      if (u * 16 + i < b) GA[u * 16 + i] = F::canon(xa[i]);
   }
   __syncthreads();
 }
