@@ -101,7 +101,7 @@ k_small_mul_batch(const BatchSmall* __restrict__ d, uint32_t n, int lmax,
 // product.  Task = (product, operand, column tile of C columns).
 // ---------------------------------------------------------------------------
 template <class F>
-__global__ void __launch_bounds__(256)
+__global__ void TFT_COL_LAUNCH_BOUNDS(256, typename F::T)
 k_col_fwd_batch(const BatchLarge* __restrict__ d, uint32_t nl, int lr,
                 int clog, RootTable<typename F::T> rt) {
   using T = typename F::T;
@@ -126,7 +126,7 @@ k_col_fwd_batch(const BatchLarge* __restrict__ d, uint32_t nl, int lr,
 
 // Phase 2: fused rows, all full rows of all products flattened.
 template <class F, int LR>
-__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
 k_row_mul_batch(const BatchLarge* __restrict__ d, uint32_t nl,
                 uint64_t total_rows, RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE(2)
@@ -150,7 +150,7 @@ k_row_mul_batch(const BatchLarge* __restrict__ d, uint32_t nl,
 
 // Phase 3: ragged last rows (forward of both operands + pointwise).
 template <class F, int LR>
-__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
 k_row_last_batch(const BatchLarge* __restrict__ d, uint32_t nl,
                  RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE(2)
@@ -179,7 +179,7 @@ k_row_last_batch(const BatchLarge* __restrict__ d, uint32_t nl,
 // of length a_p, with E_q; long_cols = 1: long columns [0, b_p) of length
 // a_p + 1.  Task = (product, tile) through the prefix cs_base / cl_base.
 template <class F>
-__global__ void __launch_bounds__(256)
+__global__ void TFT_COL_LAUNCH_BOUNDS(256, typename F::T)
 k_col_inv_batch(const BatchLarge* __restrict__ d, uint32_t nl,
                 uint64_t total, int lr, int clog, int long_cols,
                 RootTable<typename F::T> rt) {

@@ -11,6 +11,18 @@
 #pragma once
 #include "stages.cuh"
 
+// Resident CTAs per SM asked of the 256-thread column kernels, per element
+// width (3 -> 80, 4 -> 64 registers per thread; measured best on GB300).
+#ifndef TFT_COL_MIN_CTAS_64
+#define TFT_COL_MIN_CTAS_64 3
+#endif
+#ifndef TFT_COL_MIN_CTAS_32
+#define TFT_COL_MIN_CTAS_32 4
+#endif
+#define TFT_COL_LAUNCH_BOUNDS(NT, T)                                  \
+  __launch_bounds__(NT, sizeof(T) == 8 ? TFT_COL_MIN_CTAS_64          \
+                                       : TFT_COL_MIN_CTAS_32)
+
 namespace tftgb {
 
 __device__ __forceinline__ uint32_t tswz(uint32_t t, int clog) {
@@ -168,7 +180,7 @@ __device__ __forceinline__ void stage_roots(RootTable<typename F::T>* s_rt,
 }
 
 template <class F, int MAXT>
-__global__ void __launch_bounds__(MAXT)
+__global__ void TFT_COL_LAUNCH_BOUNDS(MAXT, typename F::T)
 k_col_fwd2(const typename F::T* src, uint64_t n_src, typename F::T* dst,
            typename F::T* __restrict__ E, int lr, uint64_t a, uint64_t b,
            int c, int clog, uint32_t q_begin, uint32_t q_end,
@@ -441,7 +453,7 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
 }
 
 template <class F, int MAXT>
-__global__ void __launch_bounds__(MAXT)
+__global__ void TFT_COL_LAUNCH_BOUNDS(MAXT, typename F::T)
 k_col_inv2(typename F::T* X, typename F::T* __restrict__ E, int lr,
            uint32_t m, int c, int clog, uint32_t q_begin, uint32_t q_end,
            int want_E, typename F::T omega_a_tw,

@@ -411,8 +411,13 @@ static cudaError_t set_smem(const void* fn, size_t optin) {
   cudaError_t e = cudaFuncGetAttributes(&at, fn);
   if (e != cudaSuccess) return e;
   const size_t dyn = optin > at.sharedSizeBytes ? optin - at.sharedSizeBytes : 0;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)dyn);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)dyn);
+  if (e != cudaSuccess) return e;
+  // prefer the largest shared-memory carve-out, so that as many CTAs as
+  // the registers allow can also fit their tiles
+  return cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxShared);
 }
 
 // Launch with the optional hook around it (H and s in scope).

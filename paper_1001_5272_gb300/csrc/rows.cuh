@@ -9,6 +9,16 @@
 #pragma once
 #include "stages.cuh"
 
+// Resident CTAs per SM asked of the 256-thread row kernels, per element
+// width (the register cap follows: 3 -> 80, 4 -> 64 registers per thread;
+// measured best on GB300 for the 64-bit and 32-bit fields respectively).
+#ifndef TFT_ROW_MIN_CTAS_64
+#define TFT_ROW_MIN_CTAS_64 3
+#endif
+#ifndef TFT_ROW_MIN_CTAS_32
+#define TFT_ROW_MIN_CTAS_32 4
+#endif
+
 namespace tftgb {
 
 template <int LR>
@@ -17,8 +27,12 @@ struct RowGeom {
   static constexpr int TPR = (int)(R >> 4);               // threads per row
   static constexpr int THREADS = TPR < 256 ? 256 : TPR;   // per CTA
   static constexpr int G = THREADS / TPR;                 // rows per CTA
-  // at least two CTAs per SM for 256-thread CTAs (caps registers at 128)
-  static constexpr int MIN_CTAS = THREADS <= 256 ? 2 : 1;
+  // CTAs per SM asked of 256-thread CTAs holding W-byte elements
+  template <int W>
+  static constexpr int min_ctas() {
+    return THREADS <= 256 ? (W == 8 ? TFT_ROW_MIN_CTAS_64 : TFT_ROW_MIN_CTAS_32)
+                          : 1;
+  }
   static constexpr int L0 = LR % 4 ? LR % 4 : 4;          // first stage
   static constexpr int NST = 1 + (LR - L0) / 4;           // stages
   // r_lo of stage si (stage 0 covers the top L0 levels)
@@ -203,7 +217,7 @@ __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
 // Forward rows rho < a.
 // ---------------------------------------------------------------------------
 template <class F, int LR>
-__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
 k_row_fwd2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE(1)
   T* Zrow = S.Z + ((size_t)g << LR);
@@ -237,7 +251,7 @@ k_row_fwd2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
 // Inverse rows rho < a.
 // ---------------------------------------------------------------------------
 template <class F, int LR>
-__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
 k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE(1)
   T* Zrow = S.Z + ((size_t)g << LR);
@@ -369,7 +383,7 @@ __device__ __forceinline__ void row_mul_body(
 }
 
 template <class F, int LR>
-__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
 k_row_mul2(typename F::T* out, const typename F::T* __restrict__ work,
            uint64_t a, RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE(2)
@@ -460,7 +474,7 @@ __device__ __forceinline__ void row_last_body(
 
 // Last row of one transform (TWO = false) or product (TWO = true).
 template <class F, int LR, bool TWO>
-__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::MIN_CTAS)
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
 k_row_last2(typename F::T* X, const typename F::T* __restrict__ E,
             const typename F::T* work, const typename F::T* __restrict__ EB,
             uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
