@@ -128,6 +128,25 @@ tft_status tft_polymul(tft_ctx* ctx, const void* a, uint64_t na,
                        const void* b, uint64_t nb, void* out, void* stream);
 
 /*
+ * Space-restricted product (Algorithm 3, Section 5): the same result as
+ * tft_polymul, computed in the output buffer alone.  Chunks [q, q + L) of
+ * the output (L the largest power of two with q + 2L <= r) receive the
+ * transforms of A and of B at the points omega_{q..q+L-1}, obtained by
+ * folding A(omega_q x) and B(omega_q x) modulo x^L - 1 and a forward
+ * transform of length L; the chunk's pointwise product overwrites the first
+ * half; the last positions (fewer than 2^14) come from aligned blocks of
+ * 2^15 points evaluated in the context's fixed scratch; then the in-place
+ * inverse transform of length r.  Device memory beyond out: the context's
+ * fixed scratch only (no r-word work area), so out may be as long as the
+ * library supports (r <= 2^25 for 2^64 - 2^32 + 1, r <= min(2^K, 2^27)
+ * for the 32-bit primes) whatever the context's max_len.  Arguments and
+ * errors as tft_polymul.
+ */
+tft_status tft_polymul_restricted(tft_ctx* ctx, const void* a, uint64_t na,
+                                  const void* b, uint64_t nb, void* out,
+                                  void* stream);
+
+/*
  * Batched products: many independent polymul(a, b) calls (Section 5's
  * product, each exactly as tft_polymul computes it) in a few launches.
  *
@@ -383,7 +402,7 @@ const char* tft_last_cuda_error(void);
  * spent waiting for an SM.  Profiling must be off while a stream is being captured
  * into a CUDA graph.
  */
-#define TFT_NUM_KERNEL_KINDS 11
+#define TFT_NUM_KERNEL_KINDS 12
 tft_status tft_profile_enable(tft_ctx* ctx, int enable);
 tft_status tft_profile_read(tft_ctx* ctx, double* ms, uint64_t* launches);
 const char* tft_kernel_name(int kind);

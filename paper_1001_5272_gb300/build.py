@@ -19,7 +19,8 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libtft_gb300.so")
 SOURCES = ["kernels_gold.cu", "kernels_p2013.cu", "kernels_p998.cu",
            "batch_gold.cu", "batch_p2013.cu", "batch_p998.cu",
-           "dispatch.cu", "api.cu", "batch_api.cu", "gen.cu", "server.cu"]
+           "dispatch.cu", "api.cu", "batch_api.cu", "gen.cu", "server.cu",
+           "restricted.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -606,7 +606,7 @@ const char* tft_kernel_name(int kind) {
   static const char* names[K_NUM_KINDS] = {
       "k_small",   "k_small_mul",   "k_col_fwd",     "k_row_fwd",
       "k_row_inv", "k_col_inv",     "k_lastrow_inv", "k_row_mul",
-      "k_lastrow_fwd", "k_lastrow_mul", "k_gen"};
+      "k_lastrow_fwd", "k_lastrow_mul", "k_gen", "k_fold"};
   return (kind >= 0 && kind < K_NUM_KINDS) ? names[kind] : "unknown";
 }
 

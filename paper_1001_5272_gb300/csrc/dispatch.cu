@@ -21,7 +21,14 @@ namespace tftgb {
   cudaError_t NAME##_batch(const BatchLaunch& B, const void* rt, int nsm,   \
                            cudaStream_t s, const LaunchHook* hook,          \
                            const AuxStreams* aux);                          \
-  cudaError_t NAME##_prepare_batch(size_t optin);
+  cudaError_t NAME##_prepare_batch(size_t optin);                            \
+  cudaError_t NAME##_fold(void* d0, const void* s0, uint64_t n0, void* d1,    \
+                          const void* s1, uint64_t n1, uint64_t L, int ell,   \
+                          const void* powers, int nsm, cudaStream_t s);       \
+  cudaError_t NAME##_chunk_mul(void* X, const void* Y, uint64_t L, int nsm,   \
+                               cudaStream_t s);                               \
+  cudaError_t NAME##_tail(void* X, const void* S, uint64_t Q, uint64_t lo,    \
+                          uint64_t hi, int mul, int nsm, cudaStream_t s);
 
 TFT_FIELD_DECLS(p998)
 TFT_FIELD_DECLS(p2013)
@@ -93,6 +100,31 @@ PlanSmem plan_smem(int prime, const Plan& P) {
     case 1: return p2013_plan_smem(P);
     default: return gold_plan_smem(P);
   }
+}
+
+cudaError_t launch_fold(int prime, void* d0, const void* s0, uint64_t n0,
+                        void* d1, const void* s1, uint64_t n1, uint64_t L,
+                        int ell, const void* powers, int nsm,
+                        cudaStream_t s) {
+  TFT_BY_PRIME(prime,
+               p998_fold(d0, s0, n0, d1, s1, n1, L, ell, powers, nsm, s),
+               p2013_fold(d0, s0, n0, d1, s1, n1, L, ell, powers, nsm, s),
+               gold_fold(d0, s0, n0, d1, s1, n1, L, ell, powers, nsm, s));
+}
+
+cudaError_t launch_chunk_mul(int prime, void* X, const void* Y, uint64_t L,
+                             int nsm, cudaStream_t s) {
+  TFT_BY_PRIME(prime, p998_chunk_mul(X, Y, L, nsm, s),
+               p2013_chunk_mul(X, Y, L, nsm, s),
+               gold_chunk_mul(X, Y, L, nsm, s));
+}
+
+cudaError_t launch_tail(int prime, void* X, const void* S, uint64_t Q,
+                        uint64_t lo, uint64_t hi, int mul, int nsm,
+                        cudaStream_t s) {
+  TFT_BY_PRIME(prime, p998_tail(X, S, Q, lo, hi, mul, nsm, s),
+               p2013_tail(X, S, Q, lo, hi, mul, nsm, s),
+               gold_tail(X, S, Q, lo, hi, mul, nsm, s));
 }
 
 }  // namespace tftgb

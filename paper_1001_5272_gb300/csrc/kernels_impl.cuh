@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "engine.cuh"
+#include "alg3.cuh"
 #include "batch.cuh"
 #include "cols.cuh"
 #include "rows.cuh"
@@ -605,18 +606,28 @@ struct Launch {
     return e != cudaSuccess ? e : cudaGetLastError();
   }
 
+  // Columns per tile for an inverse column set of `cols` columns: the
+  // plan's, halved while the set would give fewer tiles than SMs (the long
+  // columns are often a small set).
+  static int set_clog(const Plan& P, uint32_t cols, int nsm) {
+    int cl = P.clog;
+    while (cl > 0 && ((cols + (1u << cl) - 1) >> cl) < (uint32_t)nsm) --cl;
+    return cl;
+  }
+
   static cudaError_t inverse_tail(T* x, const Plan& P, T* E, T omega_a_tw,
-                                  const RT& rt, cudaStream_t s,
+                                  const RT& rt, int nsm, cudaStream_t s,
                                   const LaunchHook* H) {
     const uint32_t R = 1u << P.lr;
-    const uint32_t C = 1u << P.clog;
-    const size_t sm = col_smem_bytes<T>(P.c, P.clog);
     // short columns q in [b, R): length a, and E_q = C_q(omega_a)
     if (P.a > 0 && P.b < R) {
       const uint32_t qb = (uint32_t)P.b;
+      const int cl = set_clog(P, R - qb, nsm);
+      const uint32_t C = 1u << cl;
       TFT_LAUNCH(K_COL_INV,
-                 k_col_inv2<F, 256><<<(R - qb + C - 1) / C, 256, sm, s>>>(
-                     x, E, P.lr, (uint32_t)P.a, P.c, P.clog, qb, R,
+                 k_col_inv2<F, 256><<<(R - qb + C - 1) / C, 256,
+                                      col_smem_bytes<T>(P.c, cl), s>>>(
+                     x, E, P.lr, (uint32_t)P.a, P.c, cl, qb, R,
                      P.b > 0 ? 1 : 0, omega_a_tw, rt));
     }
     if (P.b > 0) {
@@ -624,9 +635,12 @@ struct Launch {
                  k_lastrow_inv<F><<<1, 512, smem_row<F>(P.lr, 1), s>>>(
                      x, E, P.lr, P.a, P.b, rt));
       const uint32_t qe = (uint32_t)P.b;
+      const int cl = set_clog(P, qe, nsm);
+      const uint32_t C = 1u << cl;
       TFT_LAUNCH(K_COL_INV,
-                 k_col_inv2<F, 256><<<(qe + C - 1) / C, 256, sm, s>>>(
-                     x, E, P.lr, (uint32_t)(P.a + 1), P.c, P.clog, 0, qe, 0,
+                 k_col_inv2<F, 256><<<(qe + C - 1) / C, 256,
+                                      col_smem_bytes<T>(P.c, cl), s>>>(
+                     x, E, P.lr, (uint32_t)(P.a + 1), P.c, cl, 0, qe, 0,
                      omega_a_tw, rt));
     }
     return cudaGetLastError();
@@ -651,7 +665,7 @@ struct Launch {
                  k_row_inv<F><<<grid, 512, smem_row<F>(P.lr, 1), s>>>(
                      x, P.lr, P.a, rt));
     }
-    return inverse_tail(x, P, E, omega_a_tw, rt, s, H);
+    return inverse_tail(x, P, E, omega_a_tw, rt, nsm, s, H);
   }
 
   static cudaError_t polymul(const T* a, uint64_t na, const T* b, uint64_t nb,
@@ -695,7 +709,7 @@ struct Launch {
       if (P.b > 0) side.join();
       if (e != cudaSuccess) return e;
     }
-    return inverse_tail(out, P, EA, omega_a_tw, rt, s, H);
+    return inverse_tail(out, P, EA, omega_a_tw, rt, nsm, s, H);
   }
   // Persistent grid: the SMs times the resident CTAs of `kernel`.
   template <class K>
@@ -819,6 +833,49 @@ static PlanSmem smem_of(const Plan& P) {
 }
 
 // ---------------------------------------------------------------------------
+// Launchers of the space-restricted product's kernels (alg3.cuh)
+// ---------------------------------------------------------------------------
+static inline uint32_t flat_grid(uint64_t work, uint64_t per_block, int nsm) {
+  const uint64_t blocks = (work + per_block - 1) / per_block;
+  const uint64_t cap = (uint64_t)nsm * 8;
+  return (uint32_t)(blocks < cap ? (blocks ? blocks : 1) : cap);
+}
+
+template <class F>
+static cudaError_t launch_fold(void* d0, const void* s0, uint64_t n0,
+                               void* d1, const void* s1, uint64_t n1,
+                               uint64_t L, int ell, const void* powers,
+                               int nsm, cudaStream_t s) {
+  using T = typename F::T;
+  const dim3 grid(flat_grid(L, (uint64_t)kFoldThreads * kFoldPerThread, nsm),
+                  d1 ? 2 : 1);
+  k_fold<F><<<grid, kFoldThreads, 0, s>>>(
+      (T*)d0, (const T*)s0, n0, (T*)d1, (const T*)s1, n1, L, ell,
+      *(const FoldPowers<T>*)powers);
+  return cudaGetLastError();
+}
+
+template <class F>
+static cudaError_t launch_chunk_mul(void* X, const void* Y, uint64_t L,
+                                   int nsm, cudaStream_t s) {
+  using T = typename F::T;
+  k_chunk_mul<F><<<flat_grid(L, 256, nsm), 256, 0, s>>>((T*)X, (const T*)Y,
+                                                         L);
+  return cudaGetLastError();
+}
+
+template <class F>
+static cudaError_t launch_tail(void* X, const void* S, uint64_t Q,
+                               uint64_t lo, uint64_t hi, int mul, int nsm,
+                               cudaStream_t s) {
+  using T = typename F::T;
+  if (hi <= lo) return cudaSuccess;
+  k_tail<F><<<flat_grid(hi - lo, 256, nsm), 256, 0, s>>>(
+      (T*)X, (const T*)S, Q, lo, hi, mul);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Per-field entry points, defined once per field in kernels_<field>.cu
 // (one translation unit per field so that they compile in parallel).
 // ---------------------------------------------------------------------------
@@ -854,6 +911,19 @@ static PlanSmem smem_of(const Plan& P) {
   PlanSmem NAME##_plan_smem(const Plan& P) { return smem_of<F>(P); }
 
 #define TFT_DEFINE_FIELD_BATCH(F, NAME)                                       \
+  cudaError_t NAME##_fold(void* d0, const void* s0, uint64_t n0, void* d1,    \
+                          const void* s1, uint64_t n1, uint64_t L, int ell,   \
+                          const void* powers, int nsm, cudaStream_t s) {      \
+    return launch_fold<F>(d0, s0, n0, d1, s1, n1, L, ell, powers, nsm, s);    \
+  }                                                                           \
+  cudaError_t NAME##_chunk_mul(void* X, const void* Y, uint64_t L, int nsm,   \
+                               cudaStream_t s) {                              \
+    return launch_chunk_mul<F>(X, Y, L, nsm, s);                              \
+  }                                                                           \
+  cudaError_t NAME##_tail(void* X, const void* S, uint64_t Q, uint64_t lo,    \
+                          uint64_t hi, int mul, int nsm, cudaStream_t s) {    \
+    return launch_tail<F>(X, S, Q, lo, hi, mul, nsm, s);                      \
+  }                                                                           \
   cudaError_t NAME##_prepare_batch(size_t optin) {                            \
     return Launch<F>::prepare_batch(optin);                                   \
   }                                                                           \

@@ -1,0 +1,146 @@
+// The space-restricted product (Algorithm 3, Section 5) on the device:
+// C = AB written into the r-word output buffer with no r-sized work area
+// (include/tft.h: tft_polymul_restricted).  Host orchestration; the kernels
+// are the field translation units' folding / chunk / tail kernels and the
+// library's forward and inverse transforms.
+//
+// As in Algorithm 3, chunk [q, q + L) with L the largest power of two such
+// that q + 2L <= r receives A^_{q..q+L-1} (fold of A(omega_q x) mod x^L - 1,
+// then a forward transform of length L), [q + L, q + 2L) receives B^ the
+// same way, and the chunk's pointwise product overwrites [q, q + L).  The
+// loop runs while L > 2^12.  What remains, [q, r) with r - q < 2^14
+// (including the last position r - 1, which Algorithm 3 evaluates by
+// Horner), is produced from aligned blocks [Q, Q + M) of M = 2^15 positions
+// (fewer when r is smaller): the fold of A(omega_Q x) mod x^M - 1 and a
+// forward transform of length M in the context's fixed scratch give A^ on
+// the whole block, which is copied to the tail positions; B^ likewise is
+// multiplied in.  The auxiliary device memory is the context's fixed
+// scratch (3 x 2^14 words) whatever r is.  Finally the in-place inverse
+// transform of length r recovers C.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "alg3.cuh"
+#include "ctx.h"
+
+using namespace tftgb;
+
+namespace {
+
+int floor_log2(uint64_t x) {
+  int l = -1;
+  while (x) {
+    x >>= 1;
+    ++l;
+  }
+  return l;
+}
+
+// omega_q^{2^b}, b <= 32, in twiddle form, laid out as FoldPowers<T>.
+void fold_powers(const PrimeInfo& pr, uint64_t q, unsigned char* out) {
+  uint64_t w = omega_s(pr, q);
+  for (int b = 0; b <= 32; ++b) {
+    const uint64_t tw = to_tw(pr, w);
+    if (pr.w == 8)
+      memcpy(out + 8 * b, &tw, 8);
+    else {
+      const uint32_t t32 = (uint32_t)tw;
+      memcpy(out + 4 * b, &t32, 4);
+    }
+    w = mulm(w, w, pr.p);
+  }
+}
+
+constexpr int kChunkLogMin = 12;  // chunks with L > 2^12 use the buffer
+constexpr int kTailLog = 15;      // tail blocks of 2^15 positions
+
+}  // namespace
+
+tft_status tft_polymul_restricted(tft_ctx* ctx, const void* a, uint64_t na,
+                                  const void* b, uint64_t nb, void* out,
+                                  void* stream) {
+  if (!ctx || !a || !b || !out || na == 0 || nb == 0) return TFT_EINVAL;
+  if (!aligned16(a) || !aligned16(b) || !aligned16(out)) return TFT_EINVAL;
+  const uint64_t r = na + nb - 1;
+  const PrimeInfo& pr = ctx->pr;
+  const size_t w = pr.w;
+  if (overlap(out, r * w, a, na * w) || overlap(out, r * w, b, nb * w))
+    return TFT_EINVAL;
+  Plan Pr;
+  if (!make_plan(ctx->prime, r, &Pr)) return TFT_ERANGE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* X = (unsigned char*)out;
+  unsigned char* scratch = (unsigned char*)ctx->scratch;
+  void* E = scratch + ((size_t)1 << kTailLog) * w;  // after the tail block
+  alignas(16) unsigned char powers[33 * 8];
+  const LaunchHook& H = ctx->hook;
+  cudaError_t e = cudaSuccess;
+  auto fold = [&](void* d0, void* d1, uint64_t L, int ell, uint64_t q) {
+    fold_powers(pr, q, powers);
+    H.before(H.user, K_FOLD, s);
+    e = launch_fold(ctx->prime, d0, a, na, d1, d1 ? b : nullptr,
+                    d1 ? nb : 0, L, ell, powers, ctx->nsm, s);
+    H.after(H.user, K_FOLD, s);
+    return e == cudaSuccess;
+  };
+  // ---- chunks in the output buffer -----------------------------------------
+  uint64_t q = 0;
+  while (q + 1 < r) {
+    const int ell = floor_log2(r - q) - 1;
+    if (ell <= kChunkLogMin) break;
+    const uint64_t L = 1ull << ell;
+    Plan PL;
+    if (!make_plan(ctx->prime, L, &PL)) return TFT_ERANGE;
+    void* XA = X + q * w;
+    void* XB = X + (q + L) * w;
+    if (!fold(XA, XB, L, ell, q)) return from_cuda(ctx, e);
+    e = launch_forward(ctx->prime, XA, L, PL, E, ctx->rt, ctx->nsm, s, &H,
+                       &ctx->aux);
+    if (e == cudaSuccess)
+      e = launch_forward(ctx->prime, XB, L, PL, E, ctx->rt, ctx->nsm, s, &H,
+                         &ctx->aux);
+    if (e != cudaSuccess) return from_cuda(ctx, e);
+    H.before(H.user, K_FOLD, s);
+    e = launch_chunk_mul(ctx->prime, XA, XB, L, ctx->nsm, s);
+    H.after(H.user, K_FOLD, s);
+    if (e != cudaSuccess) return from_cuda(ctx, e);
+    q += L;
+  }
+  // ---- tail blocks in the fixed scratch ------------------------------------
+  if (q < r) {
+    int mlog = kTailLog;
+    while (mlog > 0 && (1ull << (mlog - 1)) >= r) --mlog;  // M >= r suffices
+    const uint64_t M = 1ull << mlog;
+    Plan PM;
+    if (!make_plan(ctx->prime, M, &PM)) return TFT_ERANGE;
+    for (uint64_t Q = q & ~(M - 1); Q < r; Q += M) {
+      const uint64_t lo = Q > q ? Q : q;
+      const uint64_t hi = Q + M < r ? Q + M : r;
+      for (int op = 0; op < 2; ++op) {
+        fold_powers(pr, Q, powers);
+        H.before(H.user, K_FOLD, s);
+        e = launch_fold(ctx->prime, scratch, op ? b : a, op ? nb : na,
+                        nullptr, nullptr, 0, M, mlog, powers, ctx->nsm, s);
+        H.after(H.user, K_FOLD, s);
+        if (e == cudaSuccess)
+          e = launch_forward(ctx->prime, scratch, M, PM, E, ctx->rt,
+                             ctx->nsm, s, &H, &ctx->aux);
+        if (e == cudaSuccess) {
+          H.before(H.user, K_FOLD, s);
+          e = launch_tail(ctx->prime, X, scratch, Q, lo, hi, op, ctx->nsm,
+                          s);
+          H.after(H.user, K_FOLD, s);
+        }
+        if (e != cudaSuccess) return from_cuda(ctx, e);
+      }
+    }
+  }
+  // ---- inverse transform of length r ----------------------------------------
+  return from_cuda(
+      ctx, launch_inverse(ctx->prime, X, r, Pr, scratch,
+                          Pr.small ? 0 : to_tw(pr, omega_s(pr, Pr.a)),
+                          ctx->rt, ctx->nsm, s, &H));
+}

@@ -20,7 +20,8 @@ enum KernelKind {
   K_LASTROW_FWD = 8,   // ragged last row of a forward transform
   K_LASTROW_MUL = 9,   // ragged last row of a product (forward + pointwise)
   K_GEN = 10,          // served-request operand generator
-  K_NUM_KINDS = 11
+  K_FOLD = 11,         // space-restricted product: folding, chunk products
+  K_NUM_KINDS = 12
 };
 
 // Called around every kernel launch (may be null).
@@ -99,6 +100,19 @@ cudaError_t launch_gen_table(int prime, const GenDesc* d, uint32_t nd,
 cudaError_t launch_gen_pair(int prime, void* a, uint64_t na, void* b,
                             uint64_t nb, uint64_t request, uint64_t seed,
                             int nsm, cudaStream_t s);
+
+// Space-restricted product (Algorithm 3): folding of both operands of a
+// chunk (d1 = null: one operand), a chunk's pointwise product, and the tail
+// block's copy / product.  `powers` points at 33 words omega_q^{2^b} in
+// twiddle form (host memory, passed by value to the kernel).
+cudaError_t launch_fold(int prime, void* d0, const void* s0, uint64_t n0,
+                        void* d1, const void* s1, uint64_t n1, uint64_t L,
+                        int ell, const void* powers, int nsm, cudaStream_t s);
+cudaError_t launch_chunk_mul(int prime, void* X, const void* Y, uint64_t L,
+                             int nsm, cudaStream_t s);
+cudaError_t launch_tail(int prime, void* X, const void* S, uint64_t Q,
+                        uint64_t lo, uint64_t hi, int mul, int nsm,
+                        cudaStream_t s);
 
 cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
                            void* E, const void* rt, int nsm, cudaStream_t s,

@@ -85,6 +85,7 @@ def load():
         "tft_forward": (i32, [vp, vp, u64, u32, vp]),
         "tft_inverse": (i32, [vp, vp, u64, u32, vp]),
         "tft_polymul": (i32, [vp, vp, u64, vp, u64, vp, vp]),
+        "tft_polymul_restricted": (i32, [vp, vp, u64, vp, u64, vp, vp]),
         "tft_forward_host": (i32, [vp, vp, u64, u32, vp]),
         "tft_inverse_host": (i32, [vp, vp, u64, u32, vp]),
         "tft_polymul_host": (i32, [vp, vp, u64, vp, u64, vp, vp]),
@@ -278,6 +279,19 @@ def tft_polymul(ctx, a, b, out, stream=None):
     return out
 
 
+def tft_polymul_restricted(ctx, a, b, out, stream=None):
+    """out = a * b mod p by the space-restricted product (Algorithm 3): no
+    work area beyond out and the context's fixed scratch."""
+    if out.numel() != a.numel() + b.numel() - 1:
+        raise ValueError("out must have len(a) + len(b) - 1 elements")
+    _check(load().tft_polymul_restricted(
+        ctx.handle, _dev_ptr(a, ctx.elem_bytes, "a"), a.numel(),
+        _dev_ptr(b, ctx.elem_bytes, "b"), b.numel(),
+        _dev_ptr(out, ctx.elem_bytes, "out"), _stream_handle(stream)),
+        "tft_polymul_restricted")
+    return out
+
+
 def tft_forward_host(ctx, x, k=None, stream=None):
     ptr, n = _host_ptr(x, ctx.elem_bytes, "x")
     k = _default_k(n) if k is None else int(k)
@@ -326,7 +340,7 @@ def tft_last_error(ctx):
     return int(load().tft_last_error(ctx.handle))
 
 
-NUM_KERNEL_KINDS = 11
+NUM_KERNEL_KINDS = 12
 
 
 def kernel_name(kind):
