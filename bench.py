@@ -429,6 +429,37 @@ def run_ours(args):
             "two_buffer_device_bytes_beyond_operands":
                 2 * R_PROD * 8 + 3 * (1 << 14) * 8}
         del out_r
+        # ---- TFT product vs the padded power-of-two product ---------------
+        cmp = {}
+        for name, (sa, sb) in (("3000000x5000001", (a, b)),
+                               ("2097153x2097153",
+                                (a[:2097153], b[:2097153]))):
+            r_len = sa.numel() + sb.numel() - 1
+            N = 1 << (r_len - 1).bit_length()
+            o1 = torch.empty(r_len, dtype=torch.int64, device=dev)
+            o2 = torch.empty(r_len, dtype=torch.int64, device=dev)
+            sc = torch.empty(2 * N, dtype=torch.int64, device=dev)
+            t_tft, t_pad = [], []
+            for it in range(2 + max(3, steps // 2)):
+                for o, lst in ((o1, t_tft), (o2, t_pad)):
+                    flush.zero_()
+                    ev[0].record(stream)
+                    if o is o1:
+                        tft.tft_polymul(ctx, sa, sb, o, stream)
+                    else:
+                        tft.tft_polymul_padded(ctx, sa, sb, o, sc, stream)
+                    ev[1].record(stream)
+                    torch.cuda.synchronize()
+                    if it >= 2:
+                        lst.append(ev[0].elapsed_time(ev[1]))
+            cmp[name] = {"r": r_len, "N": N,
+                         "tft_ms": statistics.median(t_tft),
+                         "padded_ms": statistics.median(t_pad),
+                         "tft_device_words": 2 * r_len,
+                         "padded_device_words": 2 * N,
+                         "equal": bool(torch.equal(o1, o2))}
+            del o1, o2, sc
+        extra["tft_vs_padded_pow2"] = cmp
         # ---- end to end through the host-buffer entry point --------------
         out_pin = torch.empty(R_PROD, dtype=torch.int64).pin_memory()
         for _ in range(2):

@@ -128,6 +128,21 @@ tft_status tft_polymul(tft_ctx* ctx, const void* a, uint64_t na,
                        const void* b, uint64_t nb, void* out, void* stream);
 
 /*
+ * Padded power-of-two product, for comparison with the TFT product (the
+ * zero-padded FFT the TFT improves on, Section 1.2): both operands
+ * zero-extended to N = 2^ceil(lg r), transforms of length N, pointwise
+ * product, inverse of length N, then the first r coefficients copied to
+ * out.  scratch: 2N device words (16-byte aligned, not overlapping the
+ * other buffers) holding the two padded transforms.  For N at most the
+ * single-CTA size (2^13 words, 2^12 for 2^64 - 2^32 + 1) the single-CTA
+ * kernel pads inside shared memory, as tft_polymul does.  Errors as
+ * tft_polymul; TFT_ERANGE if N exceeds the supported length.
+ */
+tft_status tft_polymul_padded(tft_ctx* ctx, const void* a, uint64_t na,
+                              const void* b, uint64_t nb, void* out,
+                              void* scratch, void* stream);
+
+/*
  * Space-restricted product (Algorithm 3, Section 5): the same result as
  * tft_polymul, computed in the output buffer alone.  Chunks [q, q + L) of
  * the output (L the largest power of two with q + 2L <= r) receive the

@@ -460,6 +460,41 @@ tft_status tft_polymul(tft_ctx* ctx, const void* a, uint64_t na,
                                        &ctx->aux));
 }
 
+tft_status tft_polymul_padded(tft_ctx* ctx, const void* a, uint64_t na,
+                              const void* b, uint64_t nb, void* out,
+                              void* scratch, void* stream) {
+  if (!ctx || !a || !b || !out || !scratch || na == 0 || nb == 0)
+    return TFT_EINVAL;
+  if (!aligned16(a) || !aligned16(b) || !aligned16(out) ||
+      !aligned16(scratch))
+    return TFT_EINVAL;
+  const uint64_t r = na + nb - 1;
+  const size_t w = ctx->pr.w;
+  const uint64_t N = 1ull << ceil_log2(r);
+  if (overlap(out, r * w, a, na * w) || overlap(out, r * w, b, nb * w) ||
+      overlap(scratch, 2 * N * w, a, na * w) ||
+      overlap(scratch, 2 * N * w, b, nb * w) ||
+      overlap(scratch, 2 * N * w, out, r * w))
+    return TFT_EINVAL;
+  Plan P;
+  if (!make_plan(ctx->prime, N, &P)) return TFT_ERANGE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  unsigned char* sc = (unsigned char*)scratch;
+  unsigned char* e = (unsigned char*)ctx->scratch;
+  cudaStream_t s = (cudaStream_t)stream;
+  // both operands zero-extended to N (implicitly, by the column pass), the
+  // length-N transforms, pointwise product and inverse; then the first r
+  // coefficients (the rest are zero) to out
+  cudaError_t err = launch_polymul(ctx->prime, a, na, b, nb, sc, P,
+                                   sc + N * w, e, e + (1ull << 14) * w,
+                                   P.small ? 0 : omega_a_tw(ctx, P), ctx->rt,
+                                   ctx->nsm, s, &ctx->hook, &ctx->aux);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(out, sc, r * w, cudaMemcpyDeviceToDevice, s);
+  return from_cuda(ctx, err);
+}
+
 static tft_status host_transform(tft_ctx* ctx, void* xh, uint64_t n,
                                  uint32_t k, void* stream, bool inv) {
   if (!ctx || !xh) return TFT_EINVAL;

@@ -86,6 +86,7 @@ def load():
         "tft_inverse": (i32, [vp, vp, u64, u32, vp]),
         "tft_polymul": (i32, [vp, vp, u64, vp, u64, vp, vp]),
         "tft_polymul_restricted": (i32, [vp, vp, u64, vp, u64, vp, vp]),
+        "tft_polymul_padded": (i32, [vp, vp, u64, vp, u64, vp, vp, vp]),
         "tft_forward_host": (i32, [vp, vp, u64, u32, vp]),
         "tft_inverse_host": (i32, [vp, vp, u64, u32, vp]),
         "tft_polymul_host": (i32, [vp, vp, u64, vp, u64, vp, vp]),
@@ -289,6 +290,24 @@ def tft_polymul_restricted(ctx, a, b, out, stream=None):
         _dev_ptr(b, ctx.elem_bytes, "b"), b.numel(),
         _dev_ptr(out, ctx.elem_bytes, "out"), _stream_handle(stream)),
         "tft_polymul_restricted")
+    return out
+
+
+def tft_polymul_padded(ctx, a, b, out, scratch, stream=None):
+    """out = a * b mod p through zero-padded power-of-two transforms
+    (comparison path); scratch: CUDA tensor of 2 * 2^ceil(lg r) elements."""
+    r = a.numel() + b.numel() - 1
+    if out.numel() != r:
+        raise ValueError("out must have len(a) + len(b) - 1 elements")
+    N = 1 << (r - 1).bit_length()
+    if scratch.numel() < 2 * N:
+        raise ValueError(f"scratch needs {2 * N} elements")
+    _check(load().tft_polymul_padded(
+        ctx.handle, _dev_ptr(a, ctx.elem_bytes, "a"), a.numel(),
+        _dev_ptr(b, ctx.elem_bytes, "b"), b.numel(),
+        _dev_ptr(out, ctx.elem_bytes, "out"),
+        _dev_ptr(scratch, ctx.elem_bytes, "scratch"),
+        _stream_handle(stream)), "tft_polymul_padded")
     return out
 
 
