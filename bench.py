@@ -72,7 +72,7 @@ def parse_args():
     ap.add_argument("--served-params", default=None,
                     help="small_log,lr,clog for the served leg "
                          "(default: autotuned on a sample)")
-    ap.add_argument("--only", choices=("batched", "served"),
+    ap.add_argument("--only", choices=("batched", "served", "restricted"),
                     help="run one leg alone and print its JSON (profiling)")
     ap.add_argument("--batch-count", type=int, default=None,
                     help="products in the batched leg (default 4096)")
@@ -613,6 +613,46 @@ def batched_leg(args, tft, dev, steps):
             "matches_single_calls": ok}
 
 
+def restricted_leg(args, tft, dev, steps):
+    """The space-restricted product (Algorithm 3) on the 3,000,000 x
+    5,000,001 workload: CUDA-event time per product and the library's
+    per-kernel times of one profiled product."""
+    import numpy as np
+    import torch
+
+    from workloads import config3_inputs
+
+    a_np, b_np = config3_inputs()
+    a = torch.from_numpy(a_np.view(np.int64)).to(dev)
+    b = torch.from_numpy(b_np.view(np.int64)).to(dev)
+    out = torch.empty(R_PROD, dtype=torch.int64, device=dev)
+    ctx = tft.Context(2, dev, max_len=1 << 12)
+    for _ in range(3):
+        tft.tft_polymul_restricted(ctx, a, b, out)
+    torch.cuda.synchronize()
+    tft.tft_profile_enable(ctx, True)
+    l0 = tft.tft_launch_count(ctx)
+    tft.tft_polymul_restricted(ctx, a, b, out)
+    torch.cuda.synchronize()
+    launches = tft.tft_launch_count(ctx) - l0
+    prof = tft.tft_profile_read(ctx)
+    tft.tft_profile_enable(ctx, False)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ms = []
+    for _ in range(steps):
+        ev[0].record()
+        tft.tft_polymul_restricted(ctx, a, b, out)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms.append(ev[0].elapsed_time(ev[1]))
+    ctx.close()
+    return {"ms": statistics.median(ms),
+            "mcoeffs": R_PROD / statistics.median(ms) / 1e3,
+            "launches": launches,
+            "kernels": {k: {"ms_total": v[0], "launches": v[1]}
+                        for k, v in prof.items()}}
+
+
 def served_leg(args, tft, dev):
     """Open-loop replay of the served stream over 2^64 - 2^32 + 1: Poisson
     arrivals at 20,000 requests/s for 10 s, lengths log-uniform in
@@ -685,6 +725,13 @@ def main():
         torch.cuda.set_device(0)
         out = batched_leg(args, tft, 0, max(1, args.steps))
         print(json.dumps({"leg": "batched_p2013265921", **out}), flush=True)
+        return 0
+    if args.only == "restricted":
+        import torch
+        from paper_1001_5272_gb300 import tft
+        torch.cuda.set_device(0)
+        out = restricted_leg(args, tft, 0, max(1, args.steps))
+        print(json.dumps({"leg": "restricted_goldilocks", **out}), flush=True)
         return 0
     if args.only == "served":
         import torch

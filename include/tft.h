@@ -36,9 +36,10 @@
  * exact; results are bit-for-bit those of the definitions above.
  *
  * Memory: transforms run in place on the caller's n-word device buffer; the
- * context owns a fixed scratch of at most 3 * 2^14 words plus, for products,
- * one r-word work buffer, all reserved when the context is created.  No call
- * allocates device memory.
+ * context owns a fixed scratch of 2^18 + 2^14 words (rows of at most 2^14
+ * words for transforms and products, one 2^18-point block for the
+ * space-restricted product) plus, for products, one r-word work buffer, all
+ * reserved when the context is created.  No call allocates device memory.
  *
  * Errors: argument errors are returned synchronously and nothing is
  * launched.  Launch failures return TFT_ECUDA.  Kernels run asynchronously
@@ -149,8 +150,8 @@ tft_status tft_polymul_padded(tft_ctx* ctx, const void* a, uint64_t na,
  * transforms of A and of B at the points omega_{q..q+L-1}, obtained by
  * folding A(omega_q x) and B(omega_q x) modulo x^L - 1 and a forward
  * transform of length L; the chunk's pointwise product overwrites the first
- * half; the last positions (fewer than 2^14) come from aligned blocks of
- * 2^15 points evaluated in the context's fixed scratch; then the in-place
+ * half; the last positions (fewer than 2^18) come from aligned blocks of
+ * 2^18 points evaluated in the context's fixed scratch; then the in-place
  * inverse transform of length r.  Device memory beyond out: the context's
  * fixed scratch only (no r-word work area), so out may be as long as the
  * library supports (r <= 2^25 for 2^64 - 2^32 + 1, r <= min(2^K, 2^27)

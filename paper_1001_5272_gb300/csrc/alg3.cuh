@@ -5,9 +5,8 @@
 // A(omega_q x) mod (x^L - 1) is sum_t A_{j + tL} omega_q^{j + tL}; a forward
 // transform of length L of those L coefficients gives A(omega_q omega_s) =
 // A(omega_{q+s}) for s < L (disjoint bits, as in the proof of Proposition
-// 5.1).  Each thread folds 4 coefficients j, j + 256, ...: omega_q^j from the
-// binary powers omega_q^{2^b} (kernel parameter), then one multiply per
-// term by omega_q^L = omega_q^{2^ell}.
+// 5.1).  Twiddles omega_q^e come from the binary powers omega_q^{2^b}
+// (kernel parameter).
 #pragma once
 #include "field.cuh"
 
@@ -21,49 +20,88 @@ struct FoldPowers {
 };
 
 constexpr int kFoldThreads = 256;
-constexpr int kFoldPerThread = 4;
 
-// blockIdx.y selects the operand: (dst0, src0, n0) or (dst1, src1, n1).
+// A CTA of 8 warps folds 32 * 8 / G consecutive coefficients, G = 2^glog
+// <= 8 warps per coefficient block: lane l of warp w takes coefficient
+// j = j0 + (w / G) * 32 + l and the terms i = j + gL + t G L, t = 0, 1, ...,
+// with g = w mod G, so every load reads 32 consecutive words; the G partial
+// sums of a coefficient are added through shared memory.  Short chunks
+// (small L, many terms per coefficient) thus still fill the GPU.  A lane's
+// sum omega_q^{j + gL} sum_t src_i (omega_q^{GL})^t is taken by Horner's
+// rule from the last term down (one multiply per term); omega_q^{j + gL} =
+// omega_q^{base of the warp} * omega_q^l, the first carried from iteration
+// to iteration, the second from a 32-entry table.  blockIdx.y selects the operand:
+// (dst0, src0, n0) or (dst1, src1, n1).
 template <class F>
 __global__ void __launch_bounds__(kFoldThreads)
 k_fold(typename F::T* dst0, const typename F::T* src0, uint64_t n0,
        typename F::T* dst1, const typename F::T* src1, uint64_t n1,
-       uint64_t L, int ell, FoldPowers<typename F::T> fp) {
+       uint64_t L, int ell, int glog, FoldPowers<typename F::T> fp) {
   using T = typename F::T;
+  __shared__ T part[kFoldThreads];
+  __shared__ T lanepow[32];
   T* dst = blockIdx.y ? dst1 : dst0;
   const T* src = blockIdx.y ? src1 : src0;
   const uint64_t n = blockIdx.y ? n1 : n0;
-  const T wL = fp.w[ell];
-  const T wstep = fp.w[8];  // omega_q^256 between a thread's coefficients
-  const uint64_t span = (uint64_t)kFoldThreads * kFoldPerThread;
-  for (uint64_t base = (uint64_t)blockIdx.x * span; base < L;
-       base += (uint64_t)gridDim.x * span) {
-    const uint64_t j0 = base + threadIdx.x;
-    // omega_q^{j0} from the binary powers
-    T w = F::one_tw();
-    {
-      uint64_t bits = j0;
-      int b = 0;
-      while (bits) {
-        if (bits & 1) w = F::mul_tw(w, fp.w[b]);
-        bits >>= 1;
-        ++b;
-      }
-    }
+  const uint32_t G = 1u << glog;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t g = warp & (G - 1u);
+  const uint32_t jw = warp >> glog;          // coefficient block in the CTA
+  const uint64_t per_cta = (uint64_t)32 * (8u >> glog);
+  const T wstep = fp.w[ell + glog];          // omega_q^{L G}
+  const uint64_t stride = (uint64_t)G << ell;
+  if (threadIdx.x < 32) {
+    T v = F::one_tw();
+    for (int b = 0; b < 5; ++b)
+      if ((threadIdx.x >> b) & 1) v = F::mul_tw(v, fp.w[b]);
+    lanepow[threadIdx.x] = v;
+  }
+  __syncthreads();
+  // omega_q^e for the warp's first coefficient block e = j0 + 32 jw + g L
+  // and the step omega_q^{gridDim per_cta} between its iterations, each as a
+  // product over the exponent's set bits taken across the warp's lanes
+  // (lane b contributes omega_q^{2^b} or 1; five shuffle rounds multiply)
+  auto warp_pow = [&](uint64_t e) {
+    T v = ((e >> lane) & 1) ? fp.w[lane] : F::one_tw();
 #pragma unroll
-    for (int k = 0; k < kFoldPerThread; ++k) {
-      const uint64_t j = j0 + (uint64_t)k * kFoldThreads;
-      if (j < L) {
-        T acc = 0;
-        T wt = w;
-        for (uint64_t i = j; i < n; i += L) {
-          acc = F::add(acc, F::mul_tw(src[i], wt));
-          wt = F::mul_tw(wt, wL);
-        }
-        dst[j] = F::canon(acc);
+    for (int o = 16; o >= 1; o >>= 1)
+      v = F::mul_tw(v, (T)__shfl_xor_sync(0xffffffffu, v, o));
+    return v;  // e < 2^32: lanes 0..31 cover every bit
+  };
+  T base = warp_pow((uint64_t)blockIdx.x * per_cta + (uint64_t)jw * 32 +
+                    ((uint64_t)g << ell));
+  const T bstep = warp_pow((uint64_t)gridDim.x * per_cta);
+  for (uint64_t j0 = (uint64_t)blockIdx.x * per_cta; j0 < L;
+       j0 += (uint64_t)gridDim.x * per_cta, base = F::mul_tw(base, bstep)) {
+    const uint64_t jbase = j0 + (uint64_t)jw * 32;
+    const uint64_t j = jbase + lane;
+    const uint64_t i0 = j + ((uint64_t)g << ell);
+    T acc = 0;
+    if (j < L && i0 < n) {
+      // terms t = nt - 1 down to 0, eight loads in flight at a time
+      uint64_t nt = (n - 1 - i0) / stride + 1;
+      while (nt >= 8) {
+        T v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = src[i0 + (nt - 1 - k) * stride];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc = F::add(F::mul_tw(acc, wstep), v[k]);
+        nt -= 8;
       }
-      w = F::mul_tw(w, wstep);
+      for (; nt > 0; --nt)
+        acc = F::add(F::mul_tw(acc, wstep), src[i0 + (nt - 1) * stride]);
+      acc = F::mul_tw(acc, F::mul_tw(base, lanepow[lane]));
     }
+    if (G > 1) {
+      part[threadIdx.x] = acc;
+      __syncthreads();
+      if (g == 0) {
+        for (uint32_t k = 1; k < G; ++k)
+          acc = F::add(acc, part[threadIdx.x + 32 * k]);
+      }
+      __syncthreads();
+    }
+    if (g == 0 && j < L) dst[j] = F::canon(acc);
   }
 }
 

@@ -386,7 +386,7 @@ tft_status tft_ctx_create(tft_prime prime, int device, uint64_t max_len,
     return TFT_ECUDA;
   }
   const size_t w = pr.w;
-  if (cudaMalloc(&c->scratch, 3 * (1ull << 14) * w) != cudaSuccess ||
+  if (cudaMalloc(&c->scratch, kCtxScratchWords * w) != cudaSuccess ||
       cudaMalloc(&c->work, max_len * w) != cudaSuccess) {
     ctx_release(c);
     return TFT_ENOMEM;

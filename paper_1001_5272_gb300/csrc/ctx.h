@@ -13,6 +13,11 @@
 
 namespace tftgb {
 
+// A context's fixed device scratch, in elements: the E rows of transforms
+// and products (2^14 words each at most) and, for the space-restricted
+// product, one tail block of 2^18 points plus one row.
+constexpr size_t kCtxScratchWords = ((size_t)1 << 18) + ((size_t)1 << 14);
+
 constexpr int kProfSlots = 64;
 
 struct ProfSlot {
@@ -36,7 +41,7 @@ struct tft_ctx {
   uint32_t flags;
   PrimeInfo pr;
   alignas(16) unsigned char rt[sizeof(tftgb::RootTable<uint64_t>)];
-  void* scratch;     // 3 * 2^14 words: E / EA, EB
+  void* scratch;     // kCtxScratchWords: E / EA, EB; restricted tail
   void* work;        // max_len words (products)
   void* stage;       // 3 * max_len words (host-buffer entry points)
   tft_status sticky;

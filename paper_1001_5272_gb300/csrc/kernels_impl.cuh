@@ -532,16 +532,17 @@ struct Launch {
   // Forward column pass on the stage engine: C = 2^clog columns per CTA,
   // 16 elements per thread and stage, at most 256 threads.
   static cudaError_t cols_fwd_v2(const T* src, uint64_t n_src, T* dst, T* E,
-                                 const Plan& P, const RT& rt, cudaStream_t s,
-                                 const LaunchHook* H) {
+                                 const Plan& P, const RT& rt, int nsm,
+                                 cudaStream_t s, const LaunchHook* H) {
     const uint32_t R = 1u << P.lr;
-    const uint32_t C = 1u << P.clog;
+    const int cl = set_clog(P, R, nsm);
+    const uint32_t C = 1u << cl;
     const uint64_t units = (uint64_t)C << (P.c > 4 ? P.c - 4 : 0);
     const int th = units >= 256 ? 256 : (units < 32 ? 32 : (int)units);
-    const size_t sm = col_smem_bytes<T>(P.c, P.clog);
+    const size_t sm = col_smem_bytes<T>(P.c, cl);
     TFT_LAUNCH(K_COL_FWD, k_col_fwd2<F, 256><<<(R + C - 1) / C, th, sm, s>>>(
-                              src, n_src, dst, E, P.lr, P.a, P.b, P.c, P.clog,
-                              0, R, rt));
+                              src, n_src, dst, E, P.lr, P.a, P.b, P.c, cl, 0,
+                              R, rt));
     return cudaGetLastError();
   }
 
@@ -574,7 +575,7 @@ struct Launch {
                               x, (uint32_t)n, P.l, rt));
       return cudaGetLastError();
     }
-    cols_fwd_v2(x, n, x, E, P, rt, s, H);
+    cols_fwd_v2(x, n, x, E, P, rt, nsm, s, H);
     if (!use_v2(P)) {
       const uint64_t rows = P.a + (P.b ? 1 : 0);
       const uint32_t grid =
@@ -679,8 +680,8 @@ struct Launch {
                      a, (uint32_t)na, b, (uint32_t)nb, out, P.l, rt));
       return cudaGetLastError();
     }
-    cols_fwd_v2(a, na, out, EA, P, rt, s, H);
-    cols_fwd_v2(b, nb, work, EB, P, rt, s, H);
+    cols_fwd_v2(a, na, out, EA, P, rt, nsm, s, H);
+    cols_fwd_v2(b, nb, work, EB, P, rt, nsm, s, H);
     if (!use_v2(P)) {
       const uint64_t rows = P.a + (P.b ? 1 : 0);
       const uint32_t grid =
@@ -847,10 +848,19 @@ static cudaError_t launch_fold(void* d0, const void* s0, uint64_t n0,
                                uint64_t L, int ell, const void* powers,
                                int nsm, cudaStream_t s) {
   using T = typename F::T;
-  const dim3 grid(flat_grid(L, (uint64_t)kFoldThreads * kFoldPerThread, nsm),
-                  d1 ? 2 : 1);
+  // warps per coefficient block (1, 2, 4 or 8): enough threads to fill
+  // the GPU, at least two terms per lane
+  const uint64_t nmax = n0 > n1 ? n0 : n1;
+  const uint64_t target = (uint64_t)nsm * 2048;
+  int glog = 0;
+  while (glog < 3 && (L << glog) < target && ((nmax / L) >> glog) >= 2)
+    ++glog;
+  const uint64_t per_cta = (uint64_t)32 * (8u >> glog);
+  const uint64_t blocks = (L + per_cta - 1) / per_cta;
+  const uint64_t cap = (uint64_t)nsm * 8;
+  const dim3 grid((uint32_t)(blocks < cap ? blocks : cap), d1 ? 2 : 1);
   k_fold<F><<<grid, kFoldThreads, 0, s>>>(
-      (T*)d0, (const T*)s0, n0, (T*)d1, (const T*)s1, n1, L, ell,
+      (T*)d0, (const T*)s0, n0, (T*)d1, (const T*)s1, n1, L, ell, glog,
       *(const FoldPowers<T>*)powers);
   return cudaGetLastError();
 }

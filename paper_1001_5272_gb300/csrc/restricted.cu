@@ -8,15 +8,17 @@
 // that q + 2L <= r receives A^_{q..q+L-1} (fold of A(omega_q x) mod x^L - 1,
 // then a forward transform of length L), [q + L, q + 2L) receives B^ the
 // same way, and the chunk's pointwise product overwrites [q, q + L).  The
-// loop runs while L > 2^12.  What remains, [q, r) with r - q < 2^14
+// loop runs while L > 2^16.  What remains, [q, r) with r - q < 2^18
 // (including the last position r - 1, which Algorithm 3 evaluates by
-// Horner), is produced from aligned blocks [Q, Q + M) of M = 2^15 positions
+// Horner), is produced from aligned blocks [Q, Q + M) of M = 2^18 positions
 // (fewer when r is smaller): the fold of A(omega_Q x) mod x^M - 1 and a
 // forward transform of length M in the context's fixed scratch give A^ on
 // the whole block, which is copied to the tail positions; B^ likewise is
-// multiplied in.  The auxiliary device memory is the context's fixed
-// scratch (3 x 2^14 words) whatever r is.  Finally the in-place inverse
-// transform of length r recovers C.
+// multiplied in.  (Each short chunk would cost a fold over all of A and B
+// and two small, latency-bound transforms; one or two tail blocks replace
+// the chunks below 2^17.)  The auxiliary device memory is the context's
+// fixed scratch (2^18 + 2^14 words) whatever r is.  Finally the in-place
+// inverse transform of length r recovers C.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -52,8 +54,8 @@ void fold_powers(const PrimeInfo& pr, uint64_t q, unsigned char* out) {
   }
 }
 
-constexpr int kChunkLogMin = 12;  // chunks with L > 2^12 use the buffer
-constexpr int kTailLog = 15;      // tail blocks of 2^15 positions
+constexpr int kChunkLogMin = 16;  // chunks with L > 2^16 use the buffer
+constexpr int kTailLog = 18;      // tail blocks of 2^18 positions
 
 }  // namespace
 
@@ -74,6 +76,8 @@ tft_status tft_polymul_restricted(tft_ctx* ctx, const void* a, uint64_t na,
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* X = (unsigned char*)out;
   unsigned char* scratch = (unsigned char*)ctx->scratch;
+  static_assert(((size_t)1 << kTailLog) + ((size_t)1 << 14) <= kCtxScratchWords,
+                "tail block and row scratch must fit the context scratch");
   void* E = scratch + ((size_t)1 << kTailLog) * w;  // after the tail block
   alignas(16) unsigned char powers[33 * 8];
   const LaunchHook& H = ctx->hook;
@@ -97,11 +101,20 @@ tft_status tft_polymul_restricted(tft_ctx* ctx, const void* a, uint64_t na,
     void* XA = X + q * w;
     void* XB = X + (q + L) * w;
     if (!fold(XA, XB, L, ell, q)) return from_cuda(ctx, e);
-    e = launch_forward(ctx->prime, XA, L, PL, E, ctx->rt, ctx->nsm, s, &H,
-                       &ctx->aux);
+    // the two chunk transforms are independent: B's on the context's side
+    // stream, forked after the fold and joined before the product (b = 0 for
+    // a power-of-two length, so neither transform uses E)
+    const AuxStreams& ax = ctx->aux;
+    e = cudaEventRecord(ax.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ax.side, ax.fork, 0);
     if (e == cudaSuccess)
-      e = launch_forward(ctx->prime, XB, L, PL, E, ctx->rt, ctx->nsm, s, &H,
-                         &ctx->aux);
+      e = launch_forward(ctx->prime, XB, L, PL, E, ctx->rt, ctx->nsm,
+                         ax.side, &H, nullptr);
+    if (e == cudaSuccess)
+      e = launch_forward(ctx->prime, XA, L, PL, E, ctx->rt, ctx->nsm, s, &H,
+                         nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(ax.join, ax.side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ax.join, 0);
     if (e != cudaSuccess) return from_cuda(ctx, e);
     H.before(H.user, K_FOLD, s);
     e = launch_chunk_mul(ctx->prime, XA, XB, L, ctx->nsm, s);
