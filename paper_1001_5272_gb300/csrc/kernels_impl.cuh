@@ -680,8 +680,15 @@ struct Launch {
                      a, (uint32_t)na, b, (uint32_t)nb, out, P.l, rt));
       return cudaGetLastError();
     }
-    cols_fwd_v2(a, na, out, EA, P, rt, nsm, s, H);
-    cols_fwd_v2(b, nb, work, EB, P, rt, nsm, s, H);
+    {
+      // the two operands' column passes are independent: B's runs on the
+      // side stream next to A's
+      const SideRow side{aux, s};
+      side.fork();
+      cols_fwd_v2(b, nb, work, EB, P, rt, nsm, side.side(), H);
+      cols_fwd_v2(a, na, out, EA, P, rt, nsm, s, H);
+      side.join();
+    }
     if (!use_v2(P)) {
       const uint64_t rows = P.a + (P.b ? 1 : 0);
       const uint32_t grid =
