@@ -51,6 +51,19 @@ SM_MAX_GHZ = 2.07
 MUL32_PER_MODMUL_GOLD = 4
 
 
+# DRAM bytes (read + write) per launch of the product's kernels, from one ncu
+# capture of this workload (profiles/polymul_goldilocks_3000000x5000001_launches.md);
+# to be re-taken whenever the kernel changes.
+NCU_TRAFFIC = {"k_row_mul": 128493824 + 57775872,
+               "k_col_fwd": (27014656 + 38482688 + 43160832 + 39615744) / 2,
+               "k_col_inv": (56115968 + 6850048 + 8120832 + 1536) / 2}
+NCU_TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
+                      "on k_row_mul2 / k_col_fwd2 / k_col_inv2, this workload")
+# algorithmic bytes per launch: the row pass reads A' and B' and writes C'
+# (3 r words); a column pass reads its operand and writes r words
+ALG_BYTES = {"k_row_mul": 3 * R_PROD * 8}
+
+
 def env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -353,7 +366,10 @@ def run_ours(args):
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved,
             "peak": peak, "unit": "Tmul32/s",
             "frac": achieved / peak if achieved else None,
-            "traffic": None,
+            "traffic": NCU_TRAFFIC.get(dom),
+            "traffic_source": NCU_TRAFFIC_SOURCE if dom in NCU_TRAFFIC
+            else None,
+            "algorithmic_bytes_per_launch": ALG_BYTES.get(dom),
             "work_per_launch": {"modmuls": mm,
                                 "mul32_per_modmul": MUL32_PER_MODMUL_GOLD},
             "peak_source": "derived: 152 SMs x 64 IMAD lanes/clk x 2.07 GHz "
