@@ -52,8 +52,8 @@ MUL32_PER_MODMUL_GOLD = 4
 
 
 # DRAM bytes (read + write) per launch of the product's kernels, from one ncu
-# capture of this workload (profiles/polymul_goldilocks_3000000x5000001_launches.md);
-# to be re-taken whenever the kernel changes.
+# capture of this workload's product (dram__bytes_read.sum +
+# dram__bytes_write.sum); to be re-taken whenever the kernel changes.
 NCU_TRAFFIC = {"k_row_mul": 128493824 + 57775872,
                "k_col_fwd": (27014656 + 38482688 + 43160832 + 39615744) / 2,
                "k_col_inv": (56115968 + 6850048 + 8120832 + 1536) / 2}
