@@ -42,7 +42,7 @@ R_PROD = NA + NB - 1
 TFT_N = 2**24 + 2**20 + 12345
 P_GOLD = 2**64 - 2**32 + 1
 
-# Integer-multiply roofline (sm_103a unit counts and clock, see DESIGN.md):
+# Integer-multiply roofline (sm_103a unit counts and clock):
 # 152 SMs x 64 lanes of 32-bit IMAD per SM per clock x 2.07 GHz, and a
 # 64 x 64 -> 128-bit product needs 4 32 x 32 -> 64-bit partial products.
 SMS = 152
