@@ -202,7 +202,7 @@ typedef struct tft_polymul_desc {
 /* Batch schedule; 0 in a field means the default (32-bit primes:
  * small_log 13, lr 9, 16 columns per tile; 2^64 - 2^32 + 1: 12, 10, 4).
  * Constraints: 8 <= lr <= 12, lr <= small_log <= 13 (12 for 64-bit
- * elements), columns per tile 2^(clog_plus1 - 1) <= 16. */
+ * elements), columns per tile 2^(clog_plus1 - 1) <= 32. */
 typedef struct tft_batch_params {
   uint32_t small_log;
   uint32_t lr;

@@ -30,7 +30,7 @@ def candidates(prime):
     out = []
     for lr in range(8, 12):
         for small_log in range(max(lr, 9), small_max + 1):
-            for clog in (2, 3, 4):
+            for clog in (2, 3, 4, 5):
                 out.append({"small_log": small_log, "lr": lr, "clog": clog})
     return out
 

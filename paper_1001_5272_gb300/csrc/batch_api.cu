@@ -31,7 +31,7 @@ BatchSchedule batch_schedule(const PrimeInfo& pr,
 bool batch_schedule_valid(const PrimeInfo& pr, const BatchSchedule& S) {
   const int small_max = pr.w == 8 ? 12 : 13;
   return S.lr >= 8 && S.lr <= 12 && S.small_log >= S.lr &&
-         S.small_log <= small_max && S.clog >= 0 && S.clog <= 4 &&
+         S.small_log <= small_max && S.clog >= 0 && S.clog <= 5 &&
          S.clog <= S.lr;
 }
 

@@ -110,6 +110,7 @@ def test_batch_mixed_classes(ctxs, pr):
     {"lr": 10, "small_log": 12, "clog": 2},
     {"lr": 11, "small_log": 11, "clog": 1},
     {"lr": 12, "small_log": 12, "clog": 4},
+    {"lr": 8, "small_log": 12, "clog": 5},
 ], ids=lambda d: "lr{lr}-s{small_log}-c{clog}".format(**d))
 def test_batch_schedules(ctxs, pr, params):
     pairs = [(300, 200), (256, 1), (257, 1), (1000, 3000), (4096, 4097),
@@ -257,7 +258,7 @@ def test_batch_argument_errors(ctxs):
         # schedule out of range (row length below 2^8; small class above
         # the shared-memory bound; small class below the row length)
         for bad in ({"lr": 7}, {"lr": 13}, {"small_log": 13},
-                    {"lr": 11, "small_log": 10}, {"clog": 5}):
+                    {"lr": 11, "small_log": 10}, {"clog": 6}):
             with pytest.raises(tft.TFTError) as e:
                 tft.tft_batch_plan(ctx, [(a, b, out)], bad)
             assert e.value.status == tft.TFT_EINVAL, bad

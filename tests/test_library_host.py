@@ -153,7 +153,7 @@ def test_autotune_grid_is_admissible():
         for g in grid:
             assert 8 <= g["lr"] <= 12
             assert g["lr"] <= g["small_log"] <= (12 if pid == 2 else 13)
-            assert 0 <= g["clog"] <= 4
+            assert 0 <= g["clog"] <= 5
             tft.tft_batch_work_words(pid, [(5000, 7000)], g)
     assert autotune.mix_signature([(1, 1), (2, 3), (3, 2), (64, 65)]) == \
         "0:1,2:2,7:1"
