@@ -161,6 +161,14 @@ tft_status tft_polymul_padded(tft_ctx* ctx, const void* a, uint64_t na,
 tft_status tft_polymul_restricted(tft_ctx* ctx, const void* a, uint64_t na,
                                   const void* b, uint64_t nb, void* out,
                                   void* stream);
+/* The chunk sequence tft_polymul_restricted follows for an output of r
+ * positions (host only): *count pairs (q[i], L[i]) in processing order --
+ * Algorithm 3's loop, stopped before the first chunk with L <= 2^16 -- and
+ * *tail_start, the first position produced by the tail blocks.  TFT_ERANGE
+ * if more than `capacity` chunks (64 always suffice). */
+tft_status tft_restricted_schedule(uint64_t r, uint64_t* q, uint64_t* L,
+                                   uint32_t capacity, uint32_t* count,
+                                   uint64_t* tail_start);
 
 /*
  * Batched products: many independent polymul(a, b) calls (Section 5's
@@ -231,8 +239,8 @@ tft_status tft_polymul_batch(tft_ctx* ctx, const tft_polymul_desc* descs,
  * v = x0 + 2^32 x1 + 2^64 x2 + 2^96 x3 of Philox4x32-10 (Salmon, Moraes,
  * Dror, Shaw, SC 2011) with counter (i, operand, request mod 2^32,
  * request div 2^32) and key (seed mod 2^32, seed div 2^32).  Asynchronous
- * on `stream`.  Errors: TFT_EINVAL (null or misaligned out, n = 0,
- * operand > 1).
+ * on `stream`.  Errors: TFT_EINVAL (null or misaligned out, n = 0 or
+ * n > 2^32, operand > 1).
  */
 tft_status tft_generate(tft_ctx* ctx, uint64_t seed, uint64_t request,
                         uint32_t operand, void* out, uint64_t n, void* stream);

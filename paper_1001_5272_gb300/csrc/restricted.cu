@@ -57,7 +57,41 @@ void fold_powers(const PrimeInfo& pr, uint64_t q, unsigned char* out) {
 constexpr int kChunkLogMin = 16;  // chunks with L > 2^16 use the buffer
 constexpr int kTailLog = 18;      // tail blocks of 2^18 positions
 
+// The chunk loop of Algorithm 3 for an output of r positions: the (q, L)
+// pairs processed in the output buffer, in order, and the first tail
+// position.  Returns the number of chunks (at most 64).
+int chunk_schedule(uint64_t r, uint64_t* qs, uint64_t* Ls, uint64_t* tail) {
+  uint64_t q = 0;
+  int count = 0;
+  while (q + 1 < r) {
+    const int ell = floor_log2(r - q) - 1;  // floor(lg(r - q)) - 1
+    if (ell <= kChunkLogMin) break;
+    qs[count] = q;
+    Ls[count] = 1ull << ell;
+    ++count;
+    q += 1ull << ell;
+  }
+  *tail = q;
+  return count;
+}
+
 }  // namespace
+
+tft_status tft_restricted_schedule(uint64_t r, uint64_t* q, uint64_t* L,
+                                   uint32_t capacity, uint32_t* count,
+                                   uint64_t* tail_start) {
+  if (r == 0 || !count || !tail_start) return TFT_EINVAL;
+  uint64_t qs[64], Ls[64], tail = 0;
+  const int n = chunk_schedule(r, qs, Ls, &tail);
+  if ((uint32_t)n > capacity || (n && (!q || !L))) return TFT_ERANGE;
+  for (int i = 0; i < n; ++i) {
+    q[i] = qs[i];
+    L[i] = Ls[i];
+  }
+  *count = (uint32_t)n;
+  *tail_start = tail;
+  return TFT_OK;
+}
 
 tft_status tft_polymul_restricted(tft_ctx* ctx, const void* a, uint64_t na,
                                   const void* b, uint64_t nb, void* out,
@@ -91,16 +125,17 @@ tft_status tft_polymul_restricted(tft_ctx* ctx, const void* a, uint64_t na,
     return e == cudaSuccess;
   };
   // ---- chunks in the output buffer -----------------------------------------
-  uint64_t q = 0;
-  while (q + 1 < r) {
-    const int ell = floor_log2(r - q) - 1;
-    if (ell <= kChunkLogMin) break;
-    const uint64_t L = 1ull << ell;
+  uint64_t qs[64], Ls[64], q = 0;
+  const int nchunks = chunk_schedule(r, qs, Ls, &q);
+  for (int ci = 0; ci < nchunks; ++ci) {
+    const uint64_t L = Ls[ci];
+    const int ell = floor_log2(L);
+    const uint64_t qc = qs[ci];
     Plan PL;
     if (!make_plan(ctx->prime, L, &PL)) return TFT_ERANGE;
-    void* XA = X + q * w;
-    void* XB = X + (q + L) * w;
-    if (!fold(XA, XB, L, ell, q)) return from_cuda(ctx, e);
+    void* XA = X + qc * w;
+    void* XB = X + (qc + L) * w;
+    if (!fold(XA, XB, L, ell, qc)) return from_cuda(ctx, e);
     // the two chunk transforms are independent: B's on the context's side
     // stream, forked after the fold and joined before the product (b = 0 for
     // a power-of-two length, so neither transform uses E)
@@ -120,7 +155,6 @@ tft_status tft_polymul_restricted(tft_ctx* ctx, const void* a, uint64_t na,
     e = launch_chunk_mul(ctx->prime, XA, XB, L, ctx->nsm, s);
     H.after(H.user, K_FOLD, s);
     if (e != cudaSuccess) return from_cuda(ctx, e);
-    q += L;
   }
   // ---- tail blocks in the fixed scratch ------------------------------------
   if (q < r) {

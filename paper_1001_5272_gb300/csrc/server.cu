@@ -120,7 +120,9 @@ tft_status tft_arena_usage(tft_arena* a, uint64_t* used, uint64_t* peak,
 tft_status tft_generate(tft_ctx* ctx, uint64_t seed, uint64_t request,
                         uint32_t operand, void* out, uint64_t n,
                         void* stream) {
-  if (!ctx || !out || n == 0 || operand > 1) return TFT_EINVAL;
+  // the element index is one 32-bit counter word
+  if (!ctx || !out || n == 0 || n > (1ull << 32) || operand > 1)
+    return TFT_EINVAL;
   if (!aligned16(out)) return TFT_EINVAL;
   DeviceGuard g(ctx->device);
   if (!g.ok) return TFT_ECUDA;
@@ -565,7 +567,8 @@ tft_status tft_server_replay(tft_server* s, const tft_request* reqs,
   const PrimeInfo& pr = s->ctx->pr;
   for (uint64_t i = 0; i < count; ++i) {
     const tft_request& q = reqs[i];
-    if (q.na == 0 || q.nb == 0) return TFT_EINVAL;
+    if (q.na == 0 || q.nb == 0 || q.na > (1ull << 32) || q.nb > (1ull << 32))
+      return TFT_EINVAL;
     if (i && q.arrival_s < reqs[i - 1].arrival_s) return TFT_EINVAL;
     if (keep && keep[i] && !aligned16(keep[i])) return TFT_EINVAL;
     if (mode == TFT_SERVE_BATCHED &&

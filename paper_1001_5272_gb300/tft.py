@@ -87,6 +87,10 @@ def load():
         "tft_polymul": (i32, [vp, vp, u64, vp, u64, vp, vp]),
         "tft_polymul_restricted": (i32, [vp, vp, u64, vp, u64, vp, vp]),
         "tft_polymul_padded": (i32, [vp, vp, u64, vp, u64, vp, vp, vp]),
+        "tft_restricted_schedule": (i32, [u64, ctypes.POINTER(u64),
+                                          ctypes.POINTER(u64), u32,
+                                          ctypes.POINTER(u32),
+                                          ctypes.POINTER(u64)]),
         "tft_forward_host": (i32, [vp, vp, u64, u32, vp]),
         "tft_inverse_host": (i32, [vp, vp, u64, u32, vp]),
         "tft_polymul_host": (i32, [vp, vp, u64, vp, u64, vp, vp]),
@@ -309,6 +313,19 @@ def tft_polymul_padded(ctx, a, b, out, scratch, stream=None):
         _dev_ptr(scratch, ctx.elem_bytes, "scratch"),
         _stream_handle(stream)), "tft_polymul_padded")
     return out
+
+
+def tft_restricted_schedule(r):
+    """([(q, L), ...], tail_start) of the space-restricted product for an
+    output of r positions (host only)."""
+    q = (ctypes.c_uint64 * 64)()
+    L = (ctypes.c_uint64 * 64)()
+    n = ctypes.c_uint32()
+    tail = ctypes.c_uint64()
+    _check(load().tft_restricted_schedule(int(r), q, L, 64, ctypes.byref(n),
+                                          ctypes.byref(tail)),
+           "tft_restricted_schedule")
+    return [(q[i], L[i]) for i in range(n.value)], tail.value
 
 
 def tft_forward_host(ctx, x, k=None, stream=None):

@@ -157,3 +157,33 @@ def test_autotune_grid_is_admissible():
             tft.tft_batch_work_words(pid, [(5000, 7000)], g)
     assert autotune.mix_signature([(1, 1), (2, 3), (3, 2), (64, 65)]) == \
         "0:1,2:2,7:1"
+
+
+def test_restricted_schedule_follows_algorithm_3():
+    # the chunk loop of Algorithm 3 (Section 5), checked through the
+    # properties its proof states: the chunks partition [0, tail), L_i is a
+    # power of two dividing q_i with q_i + 2 L_i <= r and is the largest such
+    # power (so each L appears at most twice, in non-increasing order); the
+    # device stops before the first chunk with L <= 2^16, so the tail holds
+    # fewer than 2^18 positions
+    import random
+    rng = random.Random(5)
+    sizes = [1, 2, 3, 2 ** 17, 2 ** 18 - 1, 2 ** 18, 2 ** 18 + 1, 8_000_000,
+             2 ** 22 + 1, 2 ** 25] + [rng.randint(1, 2 ** 25) for _ in range(200)]
+    for r in sizes:
+        chunks, tail = tft.tft_restricted_schedule(r)
+        q = 0
+        seen = {}
+        prevL = None
+        for qi, L in chunks:
+            assert qi == q and L & (L - 1) == 0 and qi % L == 0, (r, qi, L)
+            assert qi + 2 * L <= r and qi + 4 * L > r, (r, qi, L)
+            assert L > 2 ** 16
+            assert prevL is None or L <= prevL
+            seen[L] = seen.get(L, 0) + 1
+            assert seen[L] <= 2
+            prevL = L
+            q += L
+        assert tail == q and r - tail < 2 ** 18, (r, tail)
+    with pytest.raises(tft.TFTError):
+        tft.tft_restricted_schedule(0)
