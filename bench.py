@@ -409,6 +409,15 @@ def run_ours(args):
             torch.cuda.synchronize()
             fwd_ms.append(ev[0].elapsed_time(ev[1]))
             inv_ms.append(ev[2].elapsed_time(ev[3]))
+        # per-kernel times of one profiled forward and one inverse
+        kfi = {}
+        for name, fn in (("forward", tft.tft_forward),
+                         ("inverse", tft.tft_inverse)):
+            tft.tft_profile_enable(ctx, True)
+            fn(ctx, x, 25, stream)
+            torch.cuda.synchronize()
+            kfi[name] = {k: v[0] for k, v in tft.tft_profile_read(ctx).items()}
+            tft.tft_profile_enable(ctx, False)
         ok = bool(torch.equal(x.cpu(), torch.from_numpy(x_np.view(np.int64))))
         inplace_b, padded_b = tft.tft_footprint(2, TFT_N, 25, 0)
         pin_b, ppad_b = tft.tft_footprint(2, R_PROD, 0, 1)
@@ -419,6 +428,7 @@ def run_ours(args):
                 "forward_mcoeffs": TFT_N / statistics.median(fwd_ms) / 1e3,
                 "inverse_mcoeffs": TFT_N / statistics.median(inv_ms) / 1e3,
                 "roundtrip_identity": ok,
+                "kernels_ms": kfi,
                 "device_bytes_inplace": inplace_b,
                 "device_bytes_padded_2^25": padded_b},
             "polymul_footprint": {"device_bytes_inplace": pin_b,

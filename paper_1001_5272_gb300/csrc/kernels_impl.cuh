@@ -494,7 +494,7 @@ struct Launch {
   static cudaError_t rows_fwd_v2(T* x, const Plan& P, const RT& rt, int nsm,
                                  cudaStream_t s, const LaunchHook* H) {
     TFT_LR_DISPATCH(P.lr, {
-      using Geo = RowGeom<LR>;
+      using Geo = RowGeom<LR, 256>;
       const size_t sm = row_smem_bytes<T>(LR, Geo::G, 1);
       const uint32_t grid =
           v2_grid(k_row_fwd2<F, LR>, Geo::THREADS, sm, P.a, Geo::G, nsm);
@@ -506,7 +506,7 @@ struct Launch {
   static cudaError_t rows_inv_v2(T* x, const Plan& P, const RT& rt, int nsm,
                                  cudaStream_t s, const LaunchHook* H) {
     TFT_LR_DISPATCH(P.lr, {
-      using Geo = RowGeom<LR>;
+      using Geo = RowGeom<LR, 256>;
       const size_t sm = row_smem_bytes<T>(LR, Geo::G, 1);
       const uint32_t grid =
           v2_grid(k_row_inv2<F, LR>, Geo::THREADS, sm, P.a, Geo::G, nsm);

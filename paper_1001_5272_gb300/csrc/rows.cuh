@@ -21,10 +21,17 @@
 
 namespace tftgb {
 
-template <int LR>
+// Row geometry: TPR threads per row, each holding EPT = R / TPR elements
+// (16, one unit of the widest stage; more when the row is longer than
+// 16 * TMAX), G rows per CTA of THREADS threads.  The fused product rows
+// keep one unit per thread (TMAX = 1024); the forward and inverse rows cap
+// a row at 256 threads so that several CTAs share an SM.
+template <int LR, int TMAX = 1024>
 struct RowGeom {
   static constexpr uint32_t R = 1u << LR;
-  static constexpr int TPR = (int)(R >> 4);               // threads per row
+  static constexpr int TPR =
+      (int)((R >> 4) < (uint32_t)TMAX ? (R >> 4) : TMAX);  // threads per row
+  static constexpr int EPT = (int)(R / TPR);              // elements / thread
   static constexpr int THREADS = TPR < 256 ? 256 : TPR;   // per CTA
   static constexpr int G = THREADS / TPR;                 // rows per CTA
   // CTAs per SM asked of 256-thread CTAs holding W-byte elements
@@ -114,11 +121,12 @@ __device__ __forceinline__ void fwd_stage(typename F::T* Zrow,
                                           const typename F::T* Grow, int r_lo,
                                           int t, int Tpr, typename F::T RF,
                                           const typename F::T* TLs,
-                                          const StageConsts<typename F::T>& K) {
+                                          const StageConsts<typename F::T>& K,
+                                          int ept = 16) {
   using T = typename F::T;
   constexpr int U = 1 << L;
 #pragma unroll 1
-  for (int v = 0; v < (16 >> L); ++v) {
+  for (int v = 0; v < (ept >> L); ++v) {
     const uint32_t u = (uint32_t)(v * Tpr + t);
     T x[U];
 #pragma unroll
@@ -141,11 +149,12 @@ template <class F, int L, bool SRC_GLOBAL>
 __device__ __noinline__ void fwd_stage_ab(
     typename F::T* ZA, const typename F::T* GA, typename F::T* ZB,
     const typename F::T* GB, int r_lo, int t, int Tpr, typename F::T RF,
-    const typename F::T* TLs, const StageConsts<typename F::T>& K) {
+    const typename F::T* TLs, const StageConsts<typename F::T>& K,
+    int ept = 16) {
   using T = typename F::T;
   constexpr int U = 1 << L;
 #pragma unroll 1
-  for (int v = 0; v < (16 >> L); ++v) {
+  for (int v = 0; v < (ept >> L); ++v) {
     const uint32_t u = (uint32_t)(v * Tpr + t);
     T pw[U];
     powers<F, L>(pw, F::mul_tw(RF, TLs[u >> r_lo]));
@@ -175,11 +184,12 @@ __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
                                           typename F::T* Grow, int r_lo, int t,
                                           int Tpr, typename F::T RFi,
                                           const typename F::T* TLis,
-                                          const StageConsts<typename F::T>& K) {
+                                          const StageConsts<typename F::T>& K,
+                                          int ept = 16) {
   using T = typename F::T;
   constexpr int U = 1 << L;
 #pragma unroll 1
-  for (int v = 0; v < (16 >> L); ++v) {
+  for (int v = 0; v < (ept >> L); ++v) {
     const uint32_t u = (uint32_t)(v * Tpr + t);
     T x[U];
 #pragma unroll
@@ -198,9 +208,10 @@ __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
 }
 
 // Common prologue of the row kernels: root table, constants, tables.
-#define TFT_ROW_PROLOGUE(NBUF)                                          \
+#define TFT_ROW_PROLOGUE(NBUF) TFT_ROW_PROLOGUE_G(NBUF, RowGeom<LR>)
+#define TFT_ROW_PROLOGUE_G(NBUF, ...)                                   \
   using T = typename F::T;                                              \
-  using Geo = RowGeom<LR>;                                              \
+  using Geo = __VA_ARGS__;                                              \
   extern __shared__ __align__(16) unsigned char smem_raw[];             \
   __shared__ RootTable<T> s_rt;                                         \
   copy_roots<F>(&s_rt, rt);                                             \
@@ -217,9 +228,9 @@ __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
 // Forward rows rho < a.
 // ---------------------------------------------------------------------------
 template <class F, int LR>
-__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
+__global__ void __launch_bounds__(RowGeom<LR, 256>::THREADS, RowGeom<LR, 256>::template min_ctas<sizeof(typename F::T)>())
 k_row_fwd2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
-  TFT_ROW_PROLOGUE(1)
+  TFT_ROW_PROLOGUE_G(1, RowGeom<LR, 256>)
   T* Zrow = S.Z + ((size_t)g << LR);
   for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
        rho0 += (uint64_t)gridDim.x * G) {
@@ -231,14 +242,14 @@ k_row_fwd2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
     if (active)
       fwd_stage<F, Geo::L0, true>(Zrow, Grow, Geo::r_lo(0), t, Tpr,
                                   S.RF[(g * 2) * 5], S.TL + sp.s[0].tl_off,
-                                  *S.K);
+                                  *S.K, Geo::EPT);
     __syncthreads();
 #pragma unroll 1
     for (int si = 1; si < Geo::NST; ++si) {
       if (active)
         fwd_stage<F, 4, false>(Zrow, Grow, Geo::r_lo(si), t, Tpr,
                                S.RF[(g * 2) * 5 + si],
-                               S.TL + sp.s[si].tl_off, *S.K);
+                               S.TL + sp.s[si].tl_off, *S.K, Geo::EPT);
       __syncthreads();
     }
     if (active)
@@ -251,9 +262,9 @@ k_row_fwd2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
 // Inverse rows rho < a.
 // ---------------------------------------------------------------------------
 template <class F, int LR>
-__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
+__global__ void __launch_bounds__(RowGeom<LR, 256>::THREADS, RowGeom<LR, 256>::template min_ctas<sizeof(typename F::T)>())
 k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
-  TFT_ROW_PROLOGUE(1)
+  TFT_ROW_PROLOGUE_G(1, RowGeom<LR, 256>)
   T* Zrow = S.Z + ((size_t)g << LR);
   for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
        rho0 += (uint64_t)gridDim.x * G) {
@@ -270,13 +281,13 @@ k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
       if (active)
         inv_stage<F, 4, false>(Zrow, Grow, Geo::r_lo(si), t, Tpr,
                                S.RF[(g * 2 + 1) * 5 + si],
-                               S.TLi + sp.s[si].tl_off, *S.K);
+                               S.TLi + sp.s[si].tl_off, *S.K, Geo::EPT);
       __syncthreads();
     }
     if (active)
       inv_stage<F, Geo::L0, true>(Zrow, Grow, Geo::r_lo(0), t, Tpr,
                                   S.RF[(g * 2 + 1) * 5],
-                                  S.TLi + sp.s[0].tl_off, *S.K);
+                                  S.TLi + sp.s[0].tl_off, *S.K, Geo::EPT);
     __syncthreads();
   }
 }
