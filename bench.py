@@ -496,12 +496,23 @@ def run_ours(args):
             tft.tft_polymul_host(ctx, a_pin, b_pin, out_pin, stream)
             e2e_s.append(time.perf_counter() - t0)
         same = bool(torch.equal(out_pin, out.cpu()))
+        # the link alone: one pinned H2D and one D2H copy of r words
+        cev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        cev[0].record(stream)
+        out.copy_(out_pin, non_blocking=True)
+        cev[1].record(stream)
+        out_pin.copy_(out, non_blocking=True)
+        cev[2].record(stream)
+        torch.cuda.synchronize()
+        link = {"h2d_gbs": R_PROD * 8 / cev[0].elapsed_time(cev[1]) / 1e6,
+                "d2h_gbs": R_PROD * 8 / cev[1].elapsed_time(cev[2]) / 1e6}
         e2e = {"value": R_PROD / statistics.mean(e2e_s) / 1e6,
                "unit": "Mcoeff/s",
                "h2d_bytes_per_step": (NA + NB) * 8,
                "d2h_bytes_per_step": R_PROD * 8,
                "ms_per_step": 1e3 * statistics.mean(e2e_s),
-               "matches_device_result": same}
+               "matches_device_result": same,
+               "link": link}
 
         extra["batched_p2013265921_4096"] = batched_leg(args, tft, dev,
                                                         steps)

@@ -548,11 +548,23 @@ tft_status tft_polymul_host(tft_ctx* ctx, const void* a_host, uint64_t na,
   void* da = base + slot;
   void* db = base + 2 * slot;
   cudaStream_t s = (cudaStream_t)stream;
+  // a is copied first; b follows on the side stream, where its column pass
+  // will run, so that a's column pass overlaps b's copy
+  const AuxStreams& ax = ctx->aux;
   if (cudaMemcpyAsync(da, a_host, na * w, cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
-      cudaMemcpyAsync(db, b_host, nb * w, cudaMemcpyHostToDevice, s) !=
+      cudaEventRecord(ax.fork, s) != cudaSuccess ||
+      cudaStreamWaitEvent(ax.side, ax.fork, 0) != cudaSuccess ||
+      cudaMemcpyAsync(db, b_host, nb * w, cudaMemcpyHostToDevice, ax.side) !=
           cudaSuccess)
     return from_cuda(ctx, cudaErrorUnknown);
+  Plan P;
+  if (make_plan(ctx->prime, r, &P) && P.small) {
+    // the single-CTA product reads both operands on s
+    if (cudaEventRecord(ax.join, ax.side) != cudaSuccess ||
+        cudaStreamWaitEvent(s, ax.join, 0) != cudaSuccess)
+      return from_cuda(ctx, cudaErrorUnknown);
+  }
   tft_status st = tft_polymul(ctx, da, na, db, nb, dout, stream);
   if (st != TFT_OK) {
     cudaStreamSynchronize(s);
