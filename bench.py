@@ -486,6 +486,32 @@ def run_ours(args):
                          "equal": bool(torch.equal(o1, o2))}
             del o1, o2, sc
         extra["tft_vs_padded_pow2"] = cmp
+        # the same product shape over the 32-bit prime 2013265921
+        with tft.Context(1, dev, max_len=R_PROD) as c32:
+            rng32 = np.random.default_rng(2)
+            a32 = torch.from_numpy(rng32.integers(0, 2013265921, NA,
+                                                  dtype=np.uint64).astype(
+                np.uint32).view(np.int32)).to(dev)
+            b32 = torch.from_numpy(rng32.integers(0, 2013265921, NB,
+                                                  dtype=np.uint64).astype(
+                np.uint32).view(np.int32)).to(dev)
+            o32 = torch.empty(R_PROD, dtype=torch.int32, device=dev)
+            t32 = []
+            for it in range(2 + max(3, steps // 2)):
+                flush.zero_()
+                ev[0].record(stream)
+                tft.tft_polymul(c32, a32, b32, o32, stream)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                if it >= 2:
+                    t32.append(ev[0].elapsed_time(ev[1]))
+            extra["polymul_p2013265921_3000000x5000001"] = {
+                "ms": statistics.median(t32),
+                "mcoeffs": R_PROD / statistics.median(t32) / 1e3,
+                "hbm_frac_of_algorithmic":
+                    (NA + NB + R_PROD) * 4 / (statistics.median(t32) / 1e3)
+                    / 1e9 / hbm_peak}
+            del a32, b32, o32
         # ---- end to end through the host-buffer entry point --------------
         out_pin = torch.empty(R_PROD, dtype=torch.int64).pin_memory()
         for _ in range(2):
