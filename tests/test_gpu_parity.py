@@ -33,8 +33,10 @@ def ctxs():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     tft = _lib()
+    # the largest lengths each field's plans admit (products up to r = 2^27
+    # need the work buffer of the 32-bit contexts)
     out = {pr.name: tft.Context(i, 0, max_len=(1 << 25) if pr.word_bits == 64
-                                else (1 << 26))
+                                else (1 << 27))
            for i, pr in enumerate(PRIMES)}
     yield out
     for c in out.values():
@@ -256,6 +258,25 @@ def test_config3_full_size(ctxs):
         assert int(c[t_]) == NV.conv_coeff(pr, a, b, t_), t_
 
 
+@pytest.mark.parametrize("pid,na,nb", [
+    (2, (1 << 24) + 3, (1 << 24) - 7),   # r just below 2^25: rows of 2^13
+    (1, (1 << 26) - 5, (1 << 26) + 1),   # r = 2^27 - 5: rows of 2^14
+])
+def test_polymul_longest_rows(ctxs, pid, na, nb):
+    # the largest products each field admits, which run the fused row pass
+    # on rows of 2^13 (64-bit) and 2^14 (32-bit) elements: sampled
+    # coefficients against their defining sums, and C(z) = A(z) B(z)
+    pr = PRIMES[pid]
+    a, b = rand(pr, na, 17), rand(pr, nb, 18)
+    c = gpu_polymul(ctxs, pr, a, b)
+    r = c.size
+    for t_ in [0, 1, r // 3, na - 1, nb, r - 2, r - 1]:
+        assert int(c[t_]) == NV.conv_coeff(pr, a, b, t_), t_
+    z = 987654321
+    assert NV.eval_at(pr, c, z) == \
+        NV.eval_at(pr, a, z) * NV.eval_at(pr, b, z) % pr.p
+
+
 def test_config4_subset(ctxs):
     # The batched workload's products through the single-call path
     # (every 64th product).
@@ -275,7 +296,7 @@ def test_config4_subset(ctxs):
 def test_maximum_size_roundtrip(pr, ctxs):
     # the largest length each prime and plan admit: 2^25 words for
     # 2^64 - 2^32 + 1, 2^K = 2^23 for 998244353, a ragged 2^25 + 12345 for
-    # 2013265921 (the context was created with max_len 2^26)
+    # 2013265921 (the context was created with max_len 2^27)
     tft = _lib()
     n = {"goldilocks": 1 << 25, "p998244353": 1 << 23,
          "p2013265921": (1 << 25) + 12345}[pr.name]
