@@ -44,19 +44,6 @@ __device__ __forceinline__ void load_roots(RootTable<typename F::T>* s_rt,
   __syncthreads();
 }
 
-template <class F>
-__device__ __forceinline__ typename F::T pow_tw(typename F::T base,
-                                                uint64_t e,
-                                                typename F::T one) {
-  typename F::T r = one;
-  while (e) {
-    if (e & 1) r = F::mul_tw(r, base);
-    base = F::mul_tw(base, base);
-    e >>= 1;
-  }
-  return r;
-}
-
 // ---------------------------------------------------------------------------
 // Small transforms: the whole transform of length n <= 2^l in one CTA.
 // ---------------------------------------------------------------------------
@@ -115,57 +102,6 @@ k_small_mul(const typename F::T* __restrict__ a, uint32_t na,
   inv_block<F>(Z, 0, 1, l, r, tw);
   for (uint32_t i = threadIdx.x; i < r; i += blockDim.x)
     out[i] = F::canon(Z[2 * i]);
-}
-
-// ---------------------------------------------------------------------------
-// Column pass (forward).  CTA = C consecutive columns q0 .. q0 + C - 1 of the
-// R-wide matrix view; rows t <= a.  src may differ from dst (the product
-// reads its operand and writes the output buffer); elements of src at
-// positions >= n_src are zero (the operand's zero extension).
-// ---------------------------------------------------------------------------
-template <class F>
-__global__ void __launch_bounds__(512)
-k_col_fwd(const typename F::T* src, uint64_t n_src, typename F::T* dst,
-          typename F::T* __restrict__ E, int lr, uint64_t a, uint64_t b, int c,
-          int clog, uint32_t q_begin, uint32_t q_end,
-          RootTable<typename F::T> rt) {
-  using T = typename F::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ RootTable<T> s_rt;
-  load_roots<F>(&s_rt, rt);
-  const uint32_t C = 1u << clog;
-  const uint32_t N = 1u << c;
-  T* Z = reinterpret_cast<T*>(smem_raw);
-  T* W = Z + ((size_t)N << clog);
-  build_base_tables<F>(W, nullptr, c, s_rt);
-  const uint64_t R = 1ull << lr;
-  const uint32_t q0 = q_begin + blockIdx.x * C;
-  const uint32_t total = N << clog;
-  // rows produced: a, plus row a (long columns' last value or E_q) if b > 0
-  const uint32_t rows = (uint32_t)(a + (b > 0 ? 1 : 0));
-  for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
-    const uint32_t t = i >> clog;
-    const uint64_t q = q0 + (i & (C - 1));
-    T v = 0;
-    if (q < q_end && t < rows) {
-      const uint64_t pos = q + (uint64_t)t * R;
-      if (pos < n_src) v = src[pos];
-    }
-    Z[i] = v;
-  }
-  __syncthreads();
-  fwd_pruned<F>(Z, clog, clog, c, rows, ColTw<F>{W, nullptr});
-  for (uint32_t i = threadIdx.x; i < (rows << clog); i += blockDim.x) {
-    const uint32_t t = i >> clog;
-    const uint64_t q = q0 + (i & (C - 1));
-    if (q >= q_end) continue;
-    if (t < a)
-      dst[q + (uint64_t)t * R] = F::canon(Z[i]);
-    else if (q < b)
-      dst[q + a * R] = F::canon(Z[i]);
-    else
-      E[q] = F::canon(Z[i]);
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -229,70 +165,6 @@ k_row_inv(typename F::T* X, int lr, uint64_t a, RootTable<typename F::T> rt) {
     for (uint32_t q = threadIdx.x; q < R; q += blockDim.x)
       row[q] = F::canon(Z[q]);
     __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Column pass (inverse) over columns [q_begin, q_end), all of length m
-// (m = a for short columns, a + 1 for long ones).  With want_E the kernel
-// also evaluates E_q = C_q(omega_a) by a parallel Horner rule (short
-// columns), omega_a given in twiddle form.
-// ---------------------------------------------------------------------------
-template <class F>
-__global__ void __launch_bounds__(512)
-k_col_inv(typename F::T* X, typename F::T* __restrict__ E, int lr, uint32_t m,
-          int c, int clog, uint32_t q_begin, uint32_t q_end, int want_E,
-          typename F::T omega_a_tw, RootTable<typename F::T> rt) {
-  using T = typename F::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ RootTable<T> s_rt;
-  load_roots<F>(&s_rt, rt);
-  const uint32_t C = 1u << clog;
-  const uint32_t N = 1u << c;
-  T* Z = reinterpret_cast<T*>(smem_raw);
-  T* W = Z + ((size_t)N << clog);
-  T* Wih = W + (N > 1 ? N / 2 : 1);
-  build_base_tables<F>(W, Wih, c, s_rt);
-  const uint64_t R = 1ull << lr;
-  const uint32_t q0 = q_begin + blockIdx.x * C;
-  const uint32_t total = N << clog;
-  for (uint32_t i = threadIdx.x; i < total; i += blockDim.x) {
-    const uint32_t t = i >> clog;
-    const uint64_t q = q0 + (i & (C - 1));
-    Z[i] = (q < q_end && t < m) ? X[q + (uint64_t)t * R] : T(0);
-  }
-  __syncthreads();
-  inv_block<F>(Z, clog, clog, c, m, ColTw<F>{W, Wih});
-  for (uint32_t i = threadIdx.x; i < (m << clog); i += blockDim.x) {
-    const uint32_t t = i >> clog;
-    const uint64_t q = q0 + (i & (C - 1));
-    if (q < q_end) X[q + (uint64_t)t * R] = F::canon(Z[i]);
-  }
-  if (want_E) {
-    // threads per column: blockDim / C; each takes a contiguous chunk of rows
-    const uint32_t tpc = blockDim.x >> clog;
-    const uint32_t cc = threadIdx.x & (C - 1);
-    const uint32_t k = threadIdx.x >> clog;
-    const uint32_t chunk = (m + tpc - 1) / tpc;
-    const uint32_t t0 = k * chunk;
-    uint32_t t1 = t0 + chunk;
-    if (t1 > m) t1 = m;
-    T acc = 0;
-    for (uint32_t t = t1; t > t0; --t)
-      acc = F::add(F::mul_tw(acc, omega_a_tw), Z[((t - 1) << clog) + cc]);
-    if (t0 < m) acc = F::mul_tw(acc, pow_tw<F>(omega_a_tw, t0, s_rt.one_tw));
-    else acc = 0;
-    __syncthreads();
-    T* part = W;  // reuse the table area (>= blockDim entries)
-    part[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < C) {
-      T s = 0;
-      for (uint32_t kk = 0; kk < tpc; ++kk)
-        s = F::add(s, part[(kk << clog) + threadIdx.x]);
-      const uint64_t q = q0 + threadIdx.x;
-      if (q < q_end) E[q] = F::canon(s);
-    }
   }
 }
 
@@ -459,8 +331,6 @@ struct Launch {
     if ((e = set_smem<F>((const void*)k_small<F, false>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_small<F, true>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_small_mul<F>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_col_fwd<F>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_col_inv<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_row_fwd<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_row_inv<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_row_mul<F>, mx))) return e;
