@@ -271,7 +271,10 @@ __device__ __forceinline__ void col_inv_stage_flat(
 // generalized block inverse of engine.cuh (phase A: the full inverses of the
 // dyadic blocks of m; then one descent and one ascent), with phase A on the
 // stage engine.  With want_E also E_q = C_q(omega_a) by a parallel Horner
-// rule (omega_a in twiddle form).
+// rule (omega_a in twiddle form).  Positions q + t R >= split lie past the
+// buffer: they are read from Ealt[q] and not stored (a product transform
+// whose length is rounded up to a multiple of R; its coefficients there are
+// zero).
 // ---------------------------------------------------------------------------
 template <class F>
 __device__ void col_inv_tile(unsigned char* smem_raw,
@@ -279,7 +282,9 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
                              typename F::T* X, typename F::T* E, int lr,
                              uint32_t m, int c, int clog, uint32_t q0,
                              uint32_t q_end, int want_E,
-                             typename F::T omega_a_tw) {
+                             typename F::T omega_a_tw,
+                             uint64_t split = ~0ull,
+                             const typename F::T* Ealt = nullptr) {
   using T = typename F::T;
   __syncthreads();  // the previous tile is done with shared memory
   // stage tables for 4-level stages: TL16[m'] = omega_{16 m'}, m' < 2^{c-4}
@@ -306,11 +311,44 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
   const uint64_t R = 1ull << lr;
   const uint32_t N = 1u << c;
   T* Z = S.Z;
-  for (uint32_t i = threadIdx.x; i < (N << clog); i += blockDim.x) {
-    const uint32_t t = i >> clog, cc = i & (C - 1);
-    const uint64_t q = (uint64_t)q0 + cc;
-    Z[(tswz(t, clog) << clog) + cc] =
-        (q < q_end && t < m) ? X[q + (uint64_t)t * R] : T(0);
+  // descent and ascent twiddles, one serial product per level, computed by
+  // separate threads while the tile loads: s_thd[l] = omega_{2 (m >> l)},
+  // s_tha[l] the same or (if the ascent's level l is an up step) its
+  // inverse over 2
+  __shared__ T s_thd[16], s_tha[16];
+  if (threadIdx.x >= 32 && threadIdx.x < 32 + 2 * 16) {
+    const int l = (threadIdx.x - 32) & 15;
+    const bool asc = threadIdx.x >= 48;
+    if (l >= 1 && l <= c) {
+      const uint32_t low = m & ((1u << l) - 1);
+      const bool up = asc && low >= (1u << (l - 1));
+      const T th = col_theta<F>(m >> l, s_rt, up);
+      if (asc)
+        s_tha[l] = th;
+      else
+        s_thd[l] = th;
+    }
+  }
+  // 8 independent loads in flight per thread
+  const uint32_t nld = N << clog;
+#pragma unroll 1
+  for (uint32_t i0 = threadIdx.x; i0 < nld; i0 += 8 * blockDim.x) {
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t i = i0 + k * blockDim.x;
+      const uint32_t t = i >> clog, cc = i & (C - 1);
+      const uint64_t q = (uint64_t)q0 + cc;
+      const uint64_t pos = q + (uint64_t)t * R;
+      v[k] = (i < nld && q < q_end && t < m)
+                 ? (pos < split ? X[pos] : Ealt[q])
+                 : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t i = i0 + k * blockDim.x;
+      if (i < nld) Z[(tswz(i >> clog, clog) << clog) + (i & (C - 1))] = v[k];
+    }
   }
   __syncthreads();
   // ---- phase A: full inverse of every dyadic block of m ------------------
@@ -370,9 +408,10 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
       }
       const uint32_t B = m & ~((1u << l) - 1);
       const uint32_t h = 1u << (l - 1);
-      const T th = col_theta<F>(B >> l, s_rt, false);
+      const T th = s_thd[l];
       const uint32_t j0 = low >= h ? low - h : low;
       const uint32_t cnt = (h - j0) << clog;
+#pragma unroll 4
       for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
         const uint32_t cc = i & (C - 1);
         const uint32_t jj = j0 + (i >> clog);
@@ -393,7 +432,8 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
       const uint32_t h = 1u << (l - 1);
       const uint32_t cnt = h << clog;
       const bool up = low >= h;
-      const T th = col_theta<F>(B >> l, s_rt, up);
+      const T th = s_tha[l];
+#pragma unroll 4
       for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
         const uint32_t cc = i & (C - 1);
         const uint32_t jj = i >> clog;
@@ -411,11 +451,13 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
     }
   }
   // ---- store and E ---------------------------------------------------------
+#pragma unroll 4
   for (uint32_t i = threadIdx.x; i < (m << clog); i += blockDim.x) {
     const uint32_t t = i >> clog, cc = i & (C - 1);
     const uint64_t q = (uint64_t)q0 + cc;
-    if (q < q_end)
-      X[q + (uint64_t)t * R] = F::canon(Z[(tswz(t, clog) << clog) + cc]);
+    const uint64_t pos = q + (uint64_t)t * R;
+    if (q < q_end && pos < split)
+      X[pos] = F::canon(Z[(tswz(t, clog) << clog) + cc]);
   }
   if (want_E) {
     const uint32_t tpc = blockDim.x >> clog;  // threads per column
@@ -457,13 +499,14 @@ __global__ void TFT_COL_LAUNCH_BOUNDS(MAXT, typename F::T)
 k_col_inv2(typename F::T* X, typename F::T* __restrict__ E, int lr,
            uint32_t m, int c, int clog, uint32_t q_begin, uint32_t q_end,
            int want_E, typename F::T omega_a_tw,
-           RootTable<typename F::T> rt) {
+           RootTable<typename F::T> rt, uint64_t split,
+           const typename F::T* Ealt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ RootTable<typename F::T> s_rt;
   stage_roots<F>(&s_rt, rt);
   col_inv_tile<F>(smem_raw, s_rt, X, E, lr, m, c, clog,
                   q_begin + blockIdx.x * (1u << clog), q_end, want_E,
-                  omega_a_tw);
+                  omega_a_tw, split, Ealt);
 }
 
 }  // namespace tftgb

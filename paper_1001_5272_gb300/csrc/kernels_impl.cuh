@@ -319,8 +319,6 @@ struct Launch {
     if ((e = set_smem<F>((const void*)k_row_mul2<F, LRV>, mx))) return e;  \
     if ((e = set_smem<F>((const void*)k_row_last2<F, LRV, false>, mx)))    \
       return e;                                                            \
-    if ((e = set_smem<F>((const void*)k_row_last2<F, LRV, true>, mx)))     \
-      return e;                                                            \
   } while (0)
 
   static cudaError_t prepare(size_t mx) {
@@ -385,16 +383,17 @@ struct Launch {
     });
     return cudaGetLastError();
   }
-  static cudaError_t rows_mul_v2(T* out, const T* work, const Plan& P,
-                                 const RT& rt, int nsm, cudaStream_t s,
-                                 const LaunchHook* H) {
+  static cudaError_t rows_mul_v2(T* out, const T* work, T* EA, const T* EB,
+                                 const Plan& P, const RT& rt, int nsm,
+                                 cudaStream_t s, const LaunchHook* H) {
     TFT_LR_DISPATCH(P.lr, {
       using Geo = RowGeom<LR>;
       const size_t sm = row_smem_bytes<T>(LR, Geo::G, 2);
       const uint32_t grid =
-          v2_grid(k_row_mul2<F, LR>, Geo::THREADS, sm, P.a, Geo::G, nsm);
+          v2_grid(k_row_mul2<F, LR>, Geo::THREADS, sm,
+                  P.a + (P.b > 0 ? 1 : 0), Geo::G, nsm);
       TFT_LAUNCH(K_ROW_MUL, k_row_mul2<F, LR><<<grid, Geo::THREADS, sm, s>>>(
-                                out, work, P.a, rt));
+                                out, work, EA, EB, P.a, P.b, rt));
     });
     return cudaGetLastError();
   }
@@ -499,7 +498,7 @@ struct Launch {
                  k_col_inv2<F, 256><<<(R - qb + C - 1) / C, 256,
                                       col_smem_bytes<T>(P.c, cl), s>>>(
                      x, E, P.lr, (uint32_t)P.a, P.c, cl, qb, R,
-                     P.b > 0 ? 1 : 0, omega_a_tw, rt));
+                     P.b > 0 ? 1 : 0, omega_a_tw, rt, ~0ull, nullptr));
     }
     if (P.b > 0) {
       TFT_LAUNCH(K_LASTROW_INV,
@@ -512,7 +511,7 @@ struct Launch {
                  k_col_inv2<F, 256><<<(qe + C - 1) / C, 256,
                                       col_smem_bytes<T>(P.c, cl), s>>>(
                      x, E, P.lr, (uint32_t)(P.a + 1), P.c, cl, 0, qe, 0,
-                     omega_a_tw, rt));
+                     omega_a_tw, rt, ~0ull, nullptr));
     }
     return cudaGetLastError();
   }
@@ -568,26 +567,27 @@ struct Launch {
       TFT_LAUNCH(K_ROW_MUL,
                  k_row_mul<F><<<grid, 512, smem_row<F>(P.lr, 2), s>>>(
                      out, work, EA, EB, P.lr, P.a, P.b, 0, rt));
-    } else {
-      const SideRow side{aux, s};
-      if (P.b > 0) {
-        side.fork();
-        cudaStream_t s2 = side.side();
-        TFT_LR_DISPATCH(P.lr, {
-          using Geo = RowGeom<LR>;
-          TFT_LAUNCH_ON(K_LASTROW_MUL, s2,
-                        (k_row_last2<F, LR, true><<<1, Geo::THREADS,
-                                                    row_smem_bytes<T>(
-                                                        LR, Geo::G, 2),
-                                                    s2>>>(out, EA, work, EB,
-                                                          P.a, P.b, rt)));
-        });
-      }
-      cudaError_t e = rows_mul_v2(out, work, P, rt, nsm, s, H);
-      if (P.b > 0) side.join();
-      if (e != cudaSuccess) return e;
+      return inverse_tail(out, P, EA, omega_a_tw, rt, nsm, s, H);
     }
-    return inverse_tail(out, P, EA, omega_a_tw, rt, nsm, s, H);
+    // The product's transforms have length (a + 1) R when b > 0 (r rounded
+    // up to a multiple of R; a TFT of any length >= r determines the
+    // product): the forward column pass already produced every column's
+    // entry in row a, with the positions past r in EA / EB.  The row pass
+    // then treats row a as a full row, and the inverse is one column pass of
+    // length a + 1 over all columns; no ragged last row, no E_q, no long
+    // column pass.
+    cudaError_t e = rows_mul_v2(out, work, EA, EB, P, rt, nsm, s, H);
+    if (e != cudaSuccess) return e;
+    if (P.b == 0) return inverse_tail(out, P, EA, omega_a_tw, rt, nsm, s, H);
+    const uint32_t R = 1u << P.lr;
+    const int cl = set_clog(P, R, nsm);
+    const uint32_t C = 1u << cl;
+    TFT_LAUNCH(K_COL_INV,
+               k_col_inv2<F, 256><<<(R + C - 1) / C, 256,
+                                    col_smem_bytes<T>(P.c, cl), s>>>(
+                   out, nullptr, P.lr, (uint32_t)(P.a + 1), P.c, cl, 0, R, 0,
+                   omega_a_tw, rt, P.a * (uint64_t)R + P.b, EA));
+    return cudaGetLastError();
   }
   // Persistent grid: the SMs times the resident CTAs of `kernel`.
   template <class K>

@@ -178,14 +178,16 @@ __device__ __noinline__ void fwd_stage_ab(
   }
 }
 
-// One inverse stage.  DST_GLOBAL: write to Grow instead of the shared row.
-template <class F, int L, bool DST_GLOBAL>
+// One inverse stage.  DST_GLOBAL: write to Grow instead of the shared row;
+// with SPLIT, positions p >= bsplit go to Galt[p] instead.
+template <class F, int L, bool DST_GLOBAL, bool SPLIT = false>
 __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
                                           typename F::T* Grow, int r_lo, int t,
                                           int Tpr, typename F::T RFi,
                                           const typename F::T* TLis,
                                           const StageConsts<typename F::T>& K,
-                                          int ept = 16) {
+                                          int ept = 16, uint32_t bsplit = 0,
+                                          typename F::T* Galt = nullptr) {
   using T = typename F::T;
   constexpr int U = 1 << L;
 #pragma unroll 1
@@ -199,7 +201,9 @@ __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const uint32_t p = unit_pos(u, r_lo, L, i);
-      if (DST_GLOBAL)
+      if (DST_GLOBAL && SPLIT)
+        (p < bsplit ? Grow : Galt)[p] = F::canon(x[i]);
+      else if (DST_GLOBAL)
         Grow[p] = F::canon(x[i]);
       else
         Zrow[swz(p)] = x[i];
@@ -298,13 +302,18 @@ k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
 // product and the first inverse stage share one unit in registers.  Requires
 // LR >= 8 (at least two stages).  row_mul_body processes, for every row slot
 // g of the CTA, row rho_g (GA, GB: that row of A' and B' in global memory);
-// inactive slots only take part in the barriers.
+// inactive slots only take part in the barriers.  A row whose positions
+// q >= bsplit lie beyond the buffers (the last row of a product transform
+// of length rounded up to a multiple of R) reads those positions from EAg /
+// EBg and writes them back to EAg.
 // ---------------------------------------------------------------------------
 template <class F, int LR>
 __device__ __forceinline__ void row_mul_body(
     RowSmem<typename F::T>& S, const StagePlan& sp, int g, int t,
     bool active, uint64_t rho, typename F::T* GA,
-    const typename F::T* GB, const RootTable<typename F::T>& s_rt) {
+    const typename F::T* GB, const RootTable<typename F::T>& s_rt,
+    uint32_t bsplit = 0xffffffffu, typename F::T* EAg = nullptr,
+    const typename F::T* EBg = nullptr) {
   using T = typename F::T;
   using Geo = RowGeom<LR>;
   constexpr uint32_t R = Geo::R;
@@ -320,9 +329,16 @@ __device__ __forceinline__ void row_mul_body(
   // there: reading the first stage straight from global memory lets the
   // scheduler overlap the two operands' loads and spill registers
   if (active) {
-    for (uint32_t q = t; q < R; q += Tpr) {
-      ZA[swz(q)] = GA[q];
-      ZB[swz(q)] = GB[q];
+    if (bsplit >= R) {
+      for (uint32_t q = t; q < R; q += Tpr) {
+        ZA[swz(q)] = GA[q];
+        ZB[swz(q)] = GB[q];
+      }
+    } else {
+      for (uint32_t q = t; q < R; q += Tpr) {
+        ZA[swz(q)] = q < bsplit ? GA[q] : EAg[q];
+        ZB[swz(q)] = q < bsplit ? GB[q] : EBg[q];
+      }
     }
   }
   __syncthreads();
@@ -386,23 +402,37 @@ __device__ __forceinline__ void row_mul_body(
                              S.TLi + sp.s[si].tl_off, *S.K);
     __syncthreads();
   }
-  if (active)
-    inv_stage<F, Geo::L0, true>(ZA, GA, Geo::r_lo(0), t, Tpr,
-                                S.RF[(g * 2 + 1) * 5],
-                                S.TLi + sp.s[0].tl_off, *S.K);
+  if (active) {
+    if (bsplit >= R)
+      inv_stage<F, Geo::L0, true>(ZA, GA, Geo::r_lo(0), t, Tpr,
+                                  S.RF[(g * 2 + 1) * 5],
+                                  S.TLi + sp.s[0].tl_off, *S.K);
+    else
+      inv_stage<F, Geo::L0, true, true>(ZA, GA, Geo::r_lo(0), t, Tpr,
+                                        S.RF[(g * 2 + 1) * 5],
+                                        S.TLi + sp.s[0].tl_off, *S.K, 16,
+                                        bsplit, EAg);
+  }
   __syncthreads();
 }
 
+// Rows 0 .. a - 1 of the product, and with b > 0 also row a in full: the
+// product's transforms then have length (a + 1) R >= r, and the positions
+// a R + q, q >= b, past the r-word buffers live in EA / EB (R words each;
+// the forward column pass leaves them there).
 template <class F, int LR>
 __global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
 k_row_mul2(typename F::T* out, const typename F::T* __restrict__ work,
-           uint64_t a, RootTable<typename F::T> rt) {
+           typename F::T* EA, const typename F::T* EB, uint64_t a, uint64_t b,
+           RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE(2)
-  for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
+  const uint64_t nrows = a + (b > 0 ? 1 : 0);
+  for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < nrows;
        rho0 += (uint64_t)gridDim.x * G) {
     const uint64_t rho = rho0 + g;
-    row_mul_body<F, LR>(S, sp, g, t, rho < a, rho, out + rho * R,
-                        work + rho * R, s_rt);
+    row_mul_body<F, LR>(S, sp, g, t, rho < nrows, rho, out + rho * R,
+                        work + rho * R, s_rt,
+                        rho == a ? (uint32_t)b : 0xffffffffu, EA, EB);
   }
 }
 
