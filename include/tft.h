@@ -176,10 +176,9 @@ tft_status tft_restricted_schedule(uint64_t r, uint64_t* q, uint64_t* L,
  *
  * Products with r = na + nb - 1 <= 2^small_log run one per CTA entirely in
  * shared memory; the others use the row/column split with one row length
- * 2^lr for all of them, as six launches that each cover every large product
- * (forward columns, fused rows, last rows, inverse short columns, inverse
- * last rows, inverse long columns).  Each launch is persistent over its task
- * list.
+ * 2^lr for all of them, as three launches that each cover every large
+ * product (forward columns, fused rows, inverse columns).  Each launch is
+ * persistent over its task list.
  *
  * Usage: tft_ctx_reserve_batch once (reserves the descriptor tables for up
  * to max_products and a work area of work_words elements: each large

@@ -4,10 +4,12 @@
 //   small (r <= 2^small_log): one CTA holds both operands in shared memory
 //          (the single-CTA product), one product per task;
 //   large: the row/column split with one row length R = 2^lr for the whole
-//          class (a_p, b_p, c_p per product), run as six phase launches over
-//          all large products: forward columns of both operands, fused rows,
-//          ragged last rows, inverse short columns (+ E_q), inverse last
-//          rows, inverse long columns.
+//          class (a_p, b_p, c_p per product), run as three phase launches
+//          over all large products: forward columns of both operands, fused
+//          rows, inverse columns.  As in the single product, a product with
+//          b_p > 0 runs its transforms at length (a_p + 1) R: row a_p is a
+//          full row whose positions past r_p live in EA / EB, and every
+//          column's inverse has length a_p + 1.
 // Every kernel is persistent over its flattened task list (task -> product
 // by a prefix table), so one launch per phase covers the whole batch and the
 // launch sequence can be captured into one CUDA graph.
@@ -28,14 +30,12 @@ struct BatchSmall {
 struct BatchLarge {
   uint64_t a, b, out, work, EA, EB;  // device pointers
   uint64_t na, nb;
-  uint64_t omega_a_tw;               // omega_{a_p} in twiddle form
   uint32_t A;                        // a_p = r >> lr (full rows)
   uint32_t Bm;                       // b_p = r mod R (last row length)
   uint32_t c;                        // columns padded to 2^c
   uint32_t pad;
-  uint64_t row_base;                 // prefix of A over products
-  uint64_t cs_base;                  // prefix of short-column tiles
-  uint64_t cl_base;                  // prefix of long-column tiles
+  uint64_t row_base;                 // prefix of the row counts a_p + [b_p > 0]
+  uint64_t ci_base;                  // prefix of inverse column tiles
 };
 
 // Largest p with base(p) <= x over a non-decreasing prefix (binary search).
@@ -124,7 +124,8 @@ k_col_fwd_batch(const BatchLarge* __restrict__ d, uint32_t nl, int lr,
   }
 }
 
-// Phase 2: fused rows, all full rows of all products flattened.
+// Phase 2: fused rows, all rows of all products flattened (row a_p of a
+// product with b_p > 0 reads and writes its positions past r_p in EA / EB).
 template <class F, int LR>
 __global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
 k_row_mul_batch(const BatchLarge* __restrict__ d, uint32_t nl,
@@ -137,51 +138,32 @@ k_row_mul_batch(const BatchLarge* __restrict__ d, uint32_t nl,
     uint64_t rho = 0;
     T* GA = nullptr;
     const T* GB = nullptr;
+    uint32_t bsplit = 0xffffffffu;
+    T* EA = nullptr;
+    const T* EB = nullptr;
     if (active) {
       const uint32_t p =
           find_product(nl, row, [&](uint32_t i) { return d[i].row_base; });
       rho = row - d[p].row_base;
       GA = reinterpret_cast<T*>(d[p].out) + rho * R;
       GB = reinterpret_cast<const T*>(d[p].work) + rho * R;
+      if (rho == d[p].A) {
+        bsplit = d[p].Bm;
+        EA = reinterpret_cast<T*>(d[p].EA);
+        EB = reinterpret_cast<const T*>(d[p].EB);
+      }
     }
-    row_mul_body<F, LR>(S, sp, g, t, active, rho, GA, GB, s_rt);
+    row_mul_body<F, LR>(S, sp, g, t, active, rho, GA, GB, s_rt, bsplit, EA,
+                        EB);
   }
 }
 
-// Phase 3: ragged last rows (forward of both operands + pointwise).
-template <class F, int LR>
-__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
-k_row_last_batch(const BatchLarge* __restrict__ d, uint32_t nl,
-                 RootTable<typename F::T> rt) {
-  TFT_ROW_PROLOGUE(2)
-  for (uint32_t p0 = blockIdx.x * G; p0 < nl; p0 += gridDim.x * G) {
-    const uint32_t p = p0 + g;
-    const bool active = p < nl && d[p].Bm > 0;
-    uint64_t rho = 0;
-    uint32_t bm = 0;
-    T* GA = nullptr;
-    const T *EA = nullptr, *GB = nullptr, *EB = nullptr;
-    if (active) {
-      const BatchLarge q = d[p];
-      rho = q.A;
-      bm = q.Bm;
-      GA = reinterpret_cast<T*>(q.out) + rho * R;
-      EA = reinterpret_cast<const T*>(q.EA);
-      GB = reinterpret_cast<const T*>(q.work) + rho * R;
-      EB = reinterpret_cast<const T*>(q.EB);
-    }
-    row_last_body<F, LR, true>(S, sp, g, t, active, rho, bm, GA, EA, GB, EB,
-                               s_rt);
-  }
-}
-
-// Phases 4 and 6: inverse columns.  long_cols = 0: short columns [b_p, R)
-// of length a_p, with E_q; long_cols = 1: long columns [0, b_p) of length
-// a_p + 1.  Task = (product, tile) through the prefix cs_base / cl_base.
+// Phase 3: inverse columns, all R columns of every product, of length
+// a_p + [b_p > 0].  Task = (product, tile) through the prefix ci_base.
 template <class F>
 __global__ void TFT_COL_LAUNCH_BOUNDS(256, typename F::T)
 k_col_inv_batch(const BatchLarge* __restrict__ d, uint32_t nl,
-                uint64_t total, int lr, int clog, int long_cols,
+                uint64_t total, int lr, int clog,
                 RootTable<typename F::T> rt) {
   using T = typename F::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -190,50 +172,14 @@ k_col_inv_batch(const BatchLarge* __restrict__ d, uint32_t nl,
   const uint32_t R = 1u << lr;
   const uint32_t C = 1u << clog;
   for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
-    const uint32_t p = find_product(nl, task, [&](uint32_t i) {
-      return long_cols ? d[i].cl_base : d[i].cs_base;
-    });
+    const uint32_t p =
+        find_product(nl, task, [&](uint32_t i) { return d[i].ci_base; });
     const BatchLarge q = d[p];
-    const uint32_t j =
-        (uint32_t)(task - (long_cols ? q.cl_base : q.cs_base));
-    const uint32_t q0 = (long_cols ? 0u : q.Bm) + j * C;
-    const uint32_t q_end = long_cols ? q.Bm : R;
-    col_inv_tile<F>(smem_raw, s_rt, reinterpret_cast<T*>(q.out),
-                    reinterpret_cast<T*>(q.EA), lr, long_cols ? q.A + 1 : q.A,
-                    (int)q.c, clog, q0, q_end,
-                    (!long_cols && q.Bm > 0) ? 1 : 0, (T)q.omega_a_tw);
-  }
-}
-
-// Phase 5: inverse last rows (generalized block inverse of block a_p with
-// the E_q as known inputs), one product per CTA at a time.
-template <class F>
-__global__ void __launch_bounds__(512)
-k_lastrow_inv_batch(const BatchLarge* __restrict__ d, uint32_t nl, int lr,
-                    RootTable<typename F::T> rt) {
-  using T = typename F::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ RootTable<T> s_rt;
-  stage_roots<F>(&s_rt, rt);
-  const uint32_t R = 1u << lr;
-  T* Z = reinterpret_cast<T*>(smem_raw);
-  T* W = Z + R;
-  T* Wih = W + R / 2;
-  T* L = Wih + R / 2;
-  build_base_tables<F>(W, Wih, lr, s_rt);
-  for (uint32_t p = blockIdx.x; p < nl; p += gridDim.x) {
-    const BatchLarge q = d[p];
-    if (q.Bm == 0) continue;  // uniform across the CTA
-    T* row = reinterpret_cast<T*>(q.out) + (uint64_t)q.A * R;
-    const T* E = reinterpret_cast<const T*>(q.EA);
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < R; i += blockDim.x)
-      Z[i] = i < q.Bm ? row[i] : E[i];
-    __syncthreads();
-    RowTw<F> tw{W, Wih, L, &s_rt, q.A, lr};
-    inv_block<F>(Z, 0, 0, lr, q.Bm, tw);
-    for (uint32_t i = threadIdx.x; i < q.Bm; i += blockDim.x)
-      row[i] = F::canon(Z[i]);
+    const uint32_t j = (uint32_t)(task - q.ci_base);
+    const uint64_t r = (uint64_t)q.A * R + q.Bm;
+    col_inv_tile<F>(smem_raw, s_rt, reinterpret_cast<T*>(q.out), nullptr, lr,
+                    q.A + (q.Bm > 0 ? 1u : 0u), (int)q.c, clog, j * C, R, 0,
+                    T(0), r, reinterpret_cast<const T*>(q.EA));
   }
 }
 

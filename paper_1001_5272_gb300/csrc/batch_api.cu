@@ -96,7 +96,6 @@ tft_status batch_describe(const PrimeInfo& pr, const BatchSchedule& S,
     q.out = (uint64_t)d.out;
     q.na = d.na;
     q.nb = d.nb;
-    q.omega_a_tw = to_tw(pr, omega_s(pr, q.A));
     // work area: B' (r words) then EA and EB (R words each), 16-byte slots
     unsigned char* base;
     if (work_of) {
@@ -127,14 +126,13 @@ tft_status batch_describe(const PrimeInfo& pr, const BatchSchedule& S,
             [](const BatchSmall& x, const BatchSmall& y) {
               return x.na + x.nb > y.na + y.nb;
             });
-  uint64_t rows_acc = 0, cs_acc = 0, cl_acc = 0;
+  // rows a_p (+ the full row a_p when b_p > 0), all R columns inverted
+  uint64_t rows_acc = 0, ci_acc = 0;
   for (BatchLarge& q : *hl) {
     q.row_base = rows_acc;
-    q.cs_base = cs_acc;
-    q.cl_base = cl_acc;
-    rows_acc += q.A;
-    cs_acc += (R - q.Bm + C - 1) / C;
-    cl_acc += (q.Bm + C - 1) / C;
+    q.ci_base = ci_acc;
+    rows_acc += q.A + (q.Bm ? 1 : 0);
+    ci_acc += (R + C - 1) / C;
   }
   memset(B, 0, sizeof(*B));
   B->nl = (uint32_t)hl->size();
@@ -144,8 +142,7 @@ tft_status batch_describe(const PrimeInfo& pr, const BatchSchedule& S,
   B->clog = S.clog;
   B->cmax = cmax;
   B->total_rows = rows_acc;
-  B->cs_tiles = cs_acc;
-  B->cl_tiles = cl_acc;
+  B->ci_tiles = ci_acc;
   return TFT_OK;
 }
 

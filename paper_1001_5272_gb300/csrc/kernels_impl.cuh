@@ -607,10 +607,8 @@ struct Launch {
     if ((e = set_smem<F>((const void*)k_small_mul_batch<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_col_fwd_batch<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_col_inv_batch<F>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_lastrow_inv_batch<F>, mx))) return e;
 #define TFT_PREP_BATCH_LR(LRV)                                             \
-  if ((e = set_smem<F>((const void*)k_row_mul_batch<F, LRV>, mx))) return e; \
-  if ((e = set_smem<F>((const void*)k_row_last_batch<F, LRV>, mx))) return e;
+  if ((e = set_smem<F>((const void*)k_row_mul_batch<F, LRV>, mx))) return e;
     TFT_PREP_BATCH_LR(8)
     TFT_PREP_BATCH_LR(9)
     TFT_PREP_BATCH_LR(10)
@@ -620,8 +618,8 @@ struct Launch {
     return cudaSuccess;
   }
 
-  // A planned batch: the small class on the side stream, the six phases of
-  // the large class on the caller's stream.
+  // A planned batch: the small class on the side stream, the three phases
+  // of the large class on the caller's stream.
   static cudaError_t batch(const BatchLaunch& B, const RT& rt, int nsm,
                            cudaStream_t s, const LaunchHook* H,
                            const AuxStreams* aux) {
@@ -658,38 +656,14 @@ struct Launch {
                                                  nsm),
                                              Geo::THREADS, smr, s>>>(
                        d, B.nl, B.total_rows, rt)));
-        const uint64_t lslots = (B.nl + Geo::G - 1) / Geo::G;
-        TFT_LAUNCH(K_LASTROW_MUL,
-                   (k_row_last_batch<F, LR><<<persistent_grid(
-                                                  k_row_last_batch<F, LR>,
-                                                  Geo::THREADS, smr, lslots,
-                                                  nsm),
-                                              Geo::THREADS, smr, s>>>(
-                       d, B.nl, rt)));
       });
-      if (B.cs_tiles)
+      if (B.ci_tiles)
         TFT_LAUNCH(K_COL_INV,
                    (k_col_inv_batch<F><<<persistent_grid(k_col_inv_batch<F>,
-                                                         256, smc, B.cs_tiles,
+                                                         256, smc, B.ci_tiles,
                                                          nsm),
-                                         256, smc, s>>>(d, B.nl, B.cs_tiles,
-                                                        B.lr, B.clog, 0,
-                                                        rt)));
-      const size_t sml = smem_row<F>(B.lr, 1);
-      TFT_LAUNCH(K_LASTROW_INV,
-                 (k_lastrow_inv_batch<F><<<persistent_grid(
-                                               k_lastrow_inv_batch<F>, 512,
-                                               sml, B.nl, nsm),
-                                           512, sml, s>>>(d, B.nl, B.lr,
-                                                          rt)));
-      if (B.cl_tiles)
-        TFT_LAUNCH(K_COL_INV,
-                   (k_col_inv_batch<F><<<persistent_grid(k_col_inv_batch<F>,
-                                                         256, smc, B.cl_tiles,
-                                                         nsm),
-                                         256, smc, s>>>(d, B.nl, B.cl_tiles,
-                                                        B.lr, B.clog, 1,
-                                                        rt)));
+                                         256, smc, s>>>(d, B.nl, B.ci_tiles,
+                                                        B.lr, B.clog, rt)));
     }
     if (B.ns) side.join();
     return cudaGetLastError();

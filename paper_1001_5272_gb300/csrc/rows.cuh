@@ -328,6 +328,14 @@ __device__ __forceinline__ void row_mul_body(
   // both rows to shared memory (coalesced), then the first stage from
   // there: reading the first stage straight from global memory lets the
   // scheduler overlap the two operands' loads and spill registers
+  // the split is needed again by the last stage: parked in shared memory
+  // so that it holds no registers across the stages
+  __shared__ uint32_t s_bsplit[G];
+  __shared__ T* s_ealt[G];
+  if (active && t == 0) {
+    s_bsplit[g] = bsplit;
+    s_ealt[g] = EAg;
+  }
   if (active) {
     if (bsplit >= R) {
       for (uint32_t q = t; q < R; q += Tpr) {
@@ -403,15 +411,16 @@ __device__ __forceinline__ void row_mul_body(
     __syncthreads();
   }
   if (active) {
-    if (bsplit >= R)
+    const uint32_t bs = s_bsplit[g];
+    if (bs >= R)
       inv_stage<F, Geo::L0, true>(ZA, GA, Geo::r_lo(0), t, Tpr,
                                   S.RF[(g * 2 + 1) * 5],
                                   S.TLi + sp.s[0].tl_off, *S.K);
     else
       inv_stage<F, Geo::L0, true, true>(ZA, GA, Geo::r_lo(0), t, Tpr,
                                         S.RF[(g * 2 + 1) * 5],
-                                        S.TLi + sp.s[0].tl_off, *S.K, 16,
-                                        bsplit, EAg);
+                                        S.TLi + sp.s[0].tl_off, *S.K, 16, bs,
+                                        s_ealt[g]);
   }
   __syncthreads();
 }

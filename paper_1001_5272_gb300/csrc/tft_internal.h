@@ -18,7 +18,7 @@ enum KernelKind {
   K_LASTROW_INV = 6,
   K_ROW_MUL = 7,
   K_LASTROW_FWD = 8,   // ragged last row of a forward transform
-  K_LASTROW_MUL = 9,   // ragged last row of a product (forward + pointwise)
+  K_LASTROW_MUL = 9,   // reserved: products run their last row in the row pass
   K_GEN = 10,          // served-request operand generator
   K_FOLD = 11,         // space-restricted product: folding, chunk products
   K_NUM_KINDS = 12
@@ -74,9 +74,8 @@ struct BatchLaunch {
   int lr;              // row length of the large class
   int clog;            // columns per tile
   int cmax;            // largest column log length
-  uint64_t total_rows; // sum of a_p
-  uint64_t cs_tiles;   // inverse short-column tiles
-  uint64_t cl_tiles;   // inverse long-column tiles
+  uint64_t total_rows; // sum of a_p + [b_p > 0]
+  uint64_t ci_tiles;   // inverse column tiles
 };
 
 cudaError_t launch_batch(int prime, const BatchLaunch& B, const void* rt,
