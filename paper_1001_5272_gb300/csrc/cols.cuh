@@ -135,10 +135,7 @@ __device__ void col_fwd_tile(unsigned char* smem_raw,
   __syncthreads();  // the previous tile is done with shared memory
   const StagePlan sp = make_stage_plan(c);
   ColSmem<T> S(smem_raw, sp.tl_total);
-  for (int i = threadIdx.x; i < 8; i += blockDim.x) {
-    S.K->c[i] = s_rt.c16[i];
-    S.K->ci[i] = s_rt.c16i[i];
-  }
+  fill_stage_consts<F>(S.K, s_rt, c);
   build_stage_tables<F>(S.TL, S.TLi, sp, c, s_rt);
   __syncthreads();
   const uint64_t R = 1ull << lr;
@@ -212,11 +209,14 @@ __device__ __forceinline__ typename F::T col_theta(
 // of the block covers column u mod C.  The block is block off >> k of the
 // column's network, so the stage twist is omega_{(off >> k) 2^{k - r_lo}} *
 // omega_{B_local 2^L} (inverted here, RFi is the first factor's inverse).
+// The stage returns 2^L times its exact inverse (cnet_inv2); the stage that
+// reaches the block's top level (top) multiplies by sc, the block's whole
+// factor 2^-k (times any scale its inputs carry).
 template <class F, int L>
 __device__ __forceinline__ void col_inv_unit(
     typename F::T* Z, int clog, uint32_t off, int r_lo, uint32_t u,
     typename F::T RFi, const typename F::T* TL16i,
-    const StageConsts<typename F::T>& K) {
+    const StageConsts<typename F::T>& K, bool top, typename F::T sc) {
   using T = typename F::T;
   constexpr int U = 1 << L;
   const uint32_t cc = u & ((1u << clog) - 1);
@@ -227,10 +227,14 @@ __device__ __forceinline__ void col_inv_unit(
     const uint32_t t = off + unit_pos(ut, r_lo, L, i);
     x[i] = Z[(tswz(t, clog) << clog) + cc];
   }
-  cnet_inv<F, L>(x, K);
+  cnet_inv2<F, L>(x, K);
   // only the 4-level stages below a block's top have B_local != 0
   const uint32_t bl = ut >> r_lo;
   twist<F, L>(x, L == 4 && bl ? F::mul_tw(RFi, TL16i[bl]) : RFi);
+  if (top) {
+#pragma unroll
+    for (int i = 0; i < U; ++i) x[i] = F::mul_tw(x[i], sc);
+  }
 #pragma unroll
   for (int i = 0; i < U; ++i) {
     const uint32_t t = off + unit_pos(ut, r_lo, L, i);
@@ -243,7 +247,7 @@ __device__ __forceinline__ void col_inv_unit(
 template <class F, int L>
 __device__ __forceinline__ void col_inv_stage_flat(
     typename F::T* Z, int clog, int r_lo, int j, int nb, const int* bk,
-    const uint32_t* boff, const typename F::T* rfi,
+    const uint32_t* boff, const typename F::T* rfi, const typename F::T* bsc,
     const typename F::T* TL16i, const StageConsts<typename F::T>& K) {
   uint32_t total = 0;
   for (int i = 0; i < nb; ++i) {
@@ -261,7 +265,8 @@ __device__ __forceinline__ void col_inv_stage_flat(
       if (u < cnt) break;
       u -= cnt;
     }
-    col_inv_unit<F, L>(Z, clog, boff[i], r_lo, u, rfi[j * 14 + i], TL16i, K);
+    col_inv_unit<F, L>(Z, clog, boff[i], r_lo, u, rfi[j * 14 + i], TL16i, K,
+                       bk[i] - r_lo == L, bsc[i]);
   }
 }
 
@@ -274,7 +279,9 @@ __device__ __forceinline__ void col_inv_stage_flat(
 // rule (omega_a in twiddle form).  Positions q + t R >= split lie past the
 // buffer: they are read from Ealt[q] and not stored (a product transform
 // whose length is rounded up to a multiple of R; its coefficients there are
-// zero).
+// zero).  The tile's inputs may carry a factor 2^in_scale_log (the product's
+// row pass leaves its inverse unscaled), removed here with the blocks' own
+// factors.
 // ---------------------------------------------------------------------------
 template <class F>
 __device__ void col_inv_tile(unsigned char* smem_raw,
@@ -282,7 +289,7 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
                              typename F::T* X, typename F::T* E, int lr,
                              uint32_t m, int c, int clog, uint32_t q0,
                              uint32_t q_end, int want_E,
-                             typename F::T omega_a_tw,
+                             typename F::T omega_a_tw, int in_scale_log,
                              uint64_t split = ~0ull,
                              const typename F::T* Ealt = nullptr) {
   using T = typename F::T;
@@ -290,10 +297,7 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
   // stage tables for 4-level stages: TL16[m'] = omega_{16 m'}, m' < 2^{c-4}
   const StagePlan sp = make_stage_plan(c);
   ColSmem<T> S(smem_raw, sp.tl_total);
-  for (int i = threadIdx.x; i < 8; i += blockDim.x) {
-    S.K->c[i] = s_rt.c16[i];
-    S.K->ci[i] = s_rt.c16i[i];
-  }
+  fill_stage_consts<F>(S.K, s_rt, c);
   const uint32_t n16 = c > 4 ? 1u << (c - 4) : 1u;
   T* TL16i = S.TLi;  // n16 <= tl_total entries (the last stage's table)
   for (uint32_t j = threadIdx.x; j < n16; j += blockDim.x) {
@@ -360,6 +364,7 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
   __shared__ int s_bk[14];
   __shared__ uint32_t s_boff[14];
   __shared__ T s_rfi[4 * 14];
+  __shared__ T s_bsc[14];
   __shared__ int s_nb;
   if (threadIdx.x == 0) {
     int nb = 0;
@@ -377,24 +382,34 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
   __syncthreads();
   const int nb = s_nb;
   const int nst = (c + 3) / 4;
-  for (int e = threadIdx.x; e < nst * nb; e += blockDim.x) {
+  // row factors per (stage, block), then each block's scale 2^-(k + in)
+  for (int e = threadIdx.x; e < (nst + 1) * nb; e += blockDim.x) {
     const int jj = e / nb, i = e % nb;
     const int k = s_bk[i];
-    s_rfi[jj * 14 + i] = k > 4 * jj ? row_factor<F>(s_boff[i] >> k,
-                                                    k - 4 * jj, s_rt, true)
-                                    : s_rt.one_tw;
+    if (jj == nst)
+      s_bsc[i] = pow2_inv<F>(k + in_scale_log, s_rt);
+    else
+      s_rfi[jj * 14 + i] = k > 4 * jj ? row_factor<F>(s_boff[i] >> k,
+                                                      k - 4 * jj, s_rt, true)
+                                      : s_rt.one_tw;
+  }
+  // an odd m leaves a block of one entry (row m - 1), which has no network
+  // but still carries the inputs' scale
+  if ((m & 1u) && in_scale_log > 0 && threadIdx.x < (1u << clog)) {
+    T* z = Z + (tswz(m - 1, clog) << clog) + threadIdx.x;
+    *z = F::mul_tw(*z, pow2_inv<F>(in_scale_log, s_rt));
   }
   __syncthreads();
   for (int jj = 0; jj < nst; ++jj) {
     const int r_lo = 4 * jj;
     col_inv_stage_flat<F, 4>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
-                             TL16i, *S.K);
+                             s_bsc, TL16i, *S.K);
     col_inv_stage_flat<F, 3>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
-                             TL16i, *S.K);
+                             s_bsc, TL16i, *S.K);
     col_inv_stage_flat<F, 2>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
-                             TL16i, *S.K);
+                             s_bsc, TL16i, *S.K);
     col_inv_stage_flat<F, 1>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
-                             TL16i, *S.K);
+                             s_bsc, TL16i, *S.K);
     __syncthreads();
   }
   // ---- descent and ascent (one level each) -------------------------------
@@ -498,7 +513,7 @@ template <class F, int MAXT>
 __global__ void TFT_COL_LAUNCH_BOUNDS(MAXT, typename F::T)
 k_col_inv2(typename F::T* X, typename F::T* __restrict__ E, int lr,
            uint32_t m, int c, int clog, uint32_t q_begin, uint32_t q_end,
-           int want_E, typename F::T omega_a_tw,
+           int want_E, typename F::T omega_a_tw, int in_scale_log,
            RootTable<typename F::T> rt, uint64_t split,
            const typename F::T* Ealt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -506,7 +521,7 @@ k_col_inv2(typename F::T* X, typename F::T* __restrict__ E, int lr,
   stage_roots<F>(&s_rt, rt);
   col_inv_tile<F>(smem_raw, s_rt, X, E, lr, m, c, clog,
                   q_begin + blockIdx.x * (1u << clog), q_end, want_E,
-                  omega_a_tw, split, Ealt);
+                  omega_a_tw, in_scale_log, split, Ealt);
 }
 
 }  // namespace tftgb

@@ -485,9 +485,11 @@ struct Launch {
     return cl;
   }
 
+  // in_scale_log: the rows' inverse left its factor 2^lr in x (the fused
+  // product rows); 0 when the rows are exact.
   static cudaError_t inverse_tail(T* x, const Plan& P, T* E, T omega_a_tw,
-                                  const RT& rt, int nsm, cudaStream_t s,
-                                  const LaunchHook* H) {
+                                  int in_scale_log, const RT& rt, int nsm,
+                                  cudaStream_t s, const LaunchHook* H) {
     const uint32_t R = 1u << P.lr;
     // short columns q in [b, R): length a, and E_q = C_q(omega_a)
     if (P.a > 0 && P.b < R) {
@@ -498,7 +500,8 @@ struct Launch {
                  k_col_inv2<F, 256><<<(R - qb + C - 1) / C, 256,
                                       col_smem_bytes<T>(P.c, cl), s>>>(
                      x, E, P.lr, (uint32_t)P.a, P.c, cl, qb, R,
-                     P.b > 0 ? 1 : 0, omega_a_tw, rt, ~0ull, nullptr));
+                     P.b > 0 ? 1 : 0, omega_a_tw, in_scale_log, rt, ~0ull,
+                     nullptr));
     }
     if (P.b > 0) {
       TFT_LAUNCH(K_LASTROW_INV,
@@ -511,7 +514,7 @@ struct Launch {
                  k_col_inv2<F, 256><<<(qe + C - 1) / C, 256,
                                       col_smem_bytes<T>(P.c, cl), s>>>(
                      x, E, P.lr, (uint32_t)(P.a + 1), P.c, cl, 0, qe, 0,
-                     omega_a_tw, rt, ~0ull, nullptr));
+                     omega_a_tw, in_scale_log, rt, ~0ull, nullptr));
     }
     return cudaGetLastError();
   }
@@ -535,7 +538,7 @@ struct Launch {
                  k_row_inv<F><<<grid, 512, smem_row<F>(P.lr, 1), s>>>(
                      x, P.lr, P.a, rt));
     }
-    return inverse_tail(x, P, E, omega_a_tw, rt, nsm, s, H);
+    return inverse_tail(x, P, E, omega_a_tw, 0, rt, nsm, s, H);
   }
 
   static cudaError_t polymul(const T* a, uint64_t na, const T* b, uint64_t nb,
@@ -567,7 +570,7 @@ struct Launch {
       TFT_LAUNCH(K_ROW_MUL,
                  k_row_mul<F><<<grid, 512, smem_row<F>(P.lr, 2), s>>>(
                      out, work, EA, EB, P.lr, P.a, P.b, 0, rt));
-      return inverse_tail(out, P, EA, omega_a_tw, rt, nsm, s, H);
+      return inverse_tail(out, P, EA, omega_a_tw, 0, rt, nsm, s, H);
     }
     // The product's transforms have length (a + 1) R when b > 0 (r rounded
     // up to a multiple of R; a TFT of any length >= r determines the
@@ -578,7 +581,8 @@ struct Launch {
     // column pass.
     cudaError_t e = rows_mul_v2(out, work, EA, EB, P, rt, nsm, s, H);
     if (e != cudaSuccess) return e;
-    if (P.b == 0) return inverse_tail(out, P, EA, omega_a_tw, rt, nsm, s, H);
+    if (P.b == 0)
+      return inverse_tail(out, P, EA, omega_a_tw, P.lr, rt, nsm, s, H);
     const uint32_t R = 1u << P.lr;
     const int cl = set_clog(P, R, nsm);
     const uint32_t C = 1u << cl;
@@ -586,7 +590,7 @@ struct Launch {
                k_col_inv2<F, 256><<<(R + C - 1) / C, 256,
                                     col_smem_bytes<T>(P.c, cl), s>>>(
                    out, nullptr, P.lr, (uint32_t)(P.a + 1), P.c, cl, 0, R, 0,
-                   omega_a_tw, rt, P.a * (uint64_t)R + P.b, EA));
+                   omega_a_tw, P.lr, rt, P.a * (uint64_t)R + P.b, EA));
     return cudaGetLastError();
   }
   // Persistent grid: the SMs times the resident CTAs of `kernel`.

@@ -92,10 +92,7 @@ __device__ void copy_roots(RootTable<typename F::T>* s_rt,
 template <class F>
 __device__ void row_setup(RowSmem<typename F::T>& S, const StagePlan& sp,
                           int lr, const RootTable<typename F::T>& rt) {
-  for (int i = threadIdx.x; i < 8; i += blockDim.x) {
-    S.K->c[i] = rt.c16[i];
-    S.K->ci[i] = rt.c16i[i];
-  }
+  fill_stage_consts<F>(S.K, rt, lr);
   build_stage_tables<F>(S.TL, S.TLi, sp, lr, rt);
   __syncthreads();
 }
@@ -178,9 +175,12 @@ __device__ __noinline__ void fwd_stage_ab(
   }
 }
 
-// One inverse stage.  DST_GLOBAL: write to Grow instead of the shared row;
-// with SPLIT, positions p >= bsplit go to Galt[p] instead.
-template <class F, int L, bool DST_GLOBAL, bool SPLIT = false>
+// One inverse stage (2^L times the exact inverse, see cnet_inv2).
+// DST_GLOBAL: write to Grow instead of the shared row; with SPLIT, positions
+// p >= bsplit go to Galt[p] instead; with SCALE, multiply by K.sc = 2^-lr
+// first (the last stage of a row's inverse).
+template <class F, int L, bool DST_GLOBAL, bool SPLIT = false,
+          bool SCALE = false>
 __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
                                           typename F::T* Grow, int r_lo, int t,
                                           int Tpr, typename F::T RFi,
@@ -196,8 +196,12 @@ __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
     T x[U];
 #pragma unroll
     for (int i = 0; i < U; ++i) x[i] = Zrow[swz(unit_pos(u, r_lo, L, i))];
-    cnet_inv<F, L>(x, K);
+    cnet_inv2<F, L>(x, K);
     twist<F, L>(x, F::mul_tw(RFi, TLis[u >> r_lo]));
+    if (SCALE) {
+#pragma unroll
+      for (int i = 0; i < U; ++i) x[i] = F::mul_tw(x[i], K.sc);
+    }
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const uint32_t p = unit_pos(u, r_lo, L, i);
@@ -289,16 +293,19 @@ k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
       __syncthreads();
     }
     if (active)
-      inv_stage<F, Geo::L0, true>(Zrow, Grow, Geo::r_lo(0), t, Tpr,
-                                  S.RF[(g * 2 + 1) * 5],
-                                  S.TLi + sp.s[0].tl_off, *S.K, Geo::EPT);
+      inv_stage<F, Geo::L0, true, false, true>(Zrow, Grow, Geo::r_lo(0), t,
+                                               Tpr, S.RF[(g * 2 + 1) * 5],
+                                               S.TLi + sp.s[0].tl_off, *S.K,
+                                               Geo::EPT);
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
 // Fused product rows: forward row network of A' and B', pointwise product,
-// inverse row network, result written over A'.  The last forward stage, the
+// inverse row network, result written over A'.  The inverse is left scaled
+// by 2^lr (cnet_inv2): the inverse column pass removes that factor together
+// with its own.  The last forward stage, the
 // product and the first inverse stage share one unit in registers.  Requires
 // LR >= 8 (at least two stages).  row_mul_body processes, for every row slot
 // g of the CTA, row rho_g (GA, GB: that row of A' and B' in global memory);
@@ -396,7 +403,7 @@ __device__ __forceinline__ void row_mul_body(
     cnet_fwd<F, 4>(xb, *S.K);
 #pragma unroll
     for (int i = 0; i < 16; ++i) xa[i] = F::mul_data(xa[i], xb[i]);
-    cnet_inv<F, 4>(xa, *S.K);
+    cnet_inv2<F, 4>(xa, *S.K);
     twist<F, 4>(xa, F::mul_tw(RFi, TLis[u]));
 #pragma unroll
     for (int i = 0; i < 16; ++i) ZA[swz(u * 16 + i)] = xa[i];

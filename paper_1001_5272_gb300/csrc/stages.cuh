@@ -16,10 +16,13 @@
 // omega_{B_local 2^L}; the first factor is one value per stage and row, the
 // second comes from a small per-CTA table (at most ~R/15 entries).
 //
-// The inverse stage undoes this exactly: the inverse constant network
-// (levels in increasing order, butterfly (X, Y) -> ((X+Y)/2,
-// omega_{2k}^{-1} (X-Y)/2), Algorithm 2's butterfly) and then the untwist by
-// zeta^{-i}.
+// The inverse stage undoes this up to a factor 2^L: the inverse constant
+// network (levels in increasing order, butterfly (X, Y) -> (X + Y,
+// omega_{2k}^{-1} (X - Y)), twice Algorithm 2's butterfly) and then the
+// untwist by zeta^{-i}.  Every level doubles every entry, so a whole inverse
+// of 2^k positions returns 2^k times the input; the factor 2^-k is applied
+// once, by a single multiply per entry at the end of the transform (or of a
+// block), instead of a halving in every butterfly.
 //
 // Shared memory holds a block with an XOR swizzle, phys(p) = p ^ ((p >> 4)
 // & 15), so that every stage's access pattern (unit-strided or contiguous)
@@ -73,8 +76,35 @@ __host__ __device__ inline StagePlan make_stage_plan(int lr) {
 template <class T>
 struct StageConsts {
   T c[8];    // omega_{2k}, k < 8 (twiddle form)
-  T ci[8];   // omega_{2k}^{-1} / 2 (twiddle form)
+  T cu[8];   // omega_{2k}^{-1} (twiddle form)
+  T sc;      // 2^-lr (twiddle form): the row kernels' inverse scale
 };
+
+// 2^-j in twiddle form: (1/2)^j by repeated squaring of the twiddle form of
+// 1/2 (mul_tw of two twiddle-form values is the twiddle form of their
+// product).
+template <class F>
+__device__ __forceinline__ typename F::T pow2_inv(
+    int j, const RootTable<typename F::T>& rt) {
+  typename F::T v = rt.one_tw, base = rt.half_tw;
+  for (; j; j >>= 1) {
+    if (j & 1) v = F::mul_tw(v, base);
+    base = F::mul_tw(base, base);
+  }
+  return v;
+}
+
+// The stage constants from the root table (cu[k] = 2 (omega_{2k}^{-1} / 2)).
+template <class F>
+__device__ __forceinline__ void fill_stage_consts(
+    StageConsts<typename F::T>* K, const RootTable<typename F::T>& rt,
+    int lr) {
+  for (int i = threadIdx.x; i < 8; i += blockDim.x) {
+    K->c[i] = rt.c16[i];
+    K->cu[i] = F::add(rt.c16i[i], rt.c16i[i]);
+  }
+  if (threadIdx.x == 0) K->sc = pow2_inv<F>(lr, rt);
+}
 
 // Build the local twist tables TL[m] = omega_{m 2^L} and TLi (inverses) for
 // every stage: product of omega_[b + L + 1] over the set bits b of m.
@@ -148,9 +178,11 @@ __device__ __forceinline__ void cnet_fwd(typename F::T (&x)[1 << L],
   }
 }
 
+// Inverse constant network without the halvings: returns 2^L times the
+// inputs of cnet_fwd.
 template <class F, int L>
-__device__ __forceinline__ void cnet_inv(typename F::T (&x)[1 << L],
-                                         const StageConsts<typename F::T>& K) {
+__device__ __forceinline__ void cnet_inv2(typename F::T (&x)[1 << L],
+                                          const StageConsts<typename F::T>& K) {
   using T = typename F::T;
 #pragma unroll
   for (int d = 0; d < L; ++d) {
@@ -159,9 +191,9 @@ __device__ __forceinline__ void cnet_inv(typename F::T (&x)[1 << L],
       if (i & (1 << d)) continue;
       const int k = i >> (d + 1);
       const T X = x[i], Y = x[i + (1 << d)];
-      x[i] = F::half(F::add(X, Y));
+      x[i] = F::add(X, Y);
       const T df = F::sub(X, Y);
-      x[i + (1 << d)] = k == 0 ? F::half(df) : F::mul_tw(df, K.ci[k]);
+      x[i + (1 << d)] = k == 0 ? df : F::mul_tw(df, K.cu[k]);
     }
   }
 }
