@@ -53,7 +53,7 @@ struct ColSmem {
 // its Horner reduction)
 template <class T>
 __host__ __device__ inline size_t col_smem_bytes(int c, int clog) {
-  const StagePlan sp = make_stage_plan(c);
+  const StagePlan sp = make_stage_plan(c, true);
   size_t b = sizeof(StageConsts<T>) + sizeof(T) * 2 * sp.tl_total;
   b = (b + 15) & ~(size_t)15;
   const size_t tile = (size_t)1 << (c + clog);
@@ -133,7 +133,7 @@ __device__ void col_fwd_tile(unsigned char* smem_raw,
                              uint32_t q0, uint32_t q_end) {
   using T = typename F::T;
   __syncthreads();  // the previous tile is done with shared memory
-  const StagePlan sp = make_stage_plan(c);
+  const StagePlan sp = make_stage_plan(c, true);
   ColSmem<T> S(smem_raw, sp.tl_total);
   fill_stage_consts<F>(S.K, s_rt, c);
   build_stage_tables<F>(S.TL, S.TLi, sp, c, s_rt);
@@ -295,7 +295,7 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
   using T = typename F::T;
   __syncthreads();  // the previous tile is done with shared memory
   // stage tables for 4-level stages: TL16[m'] = omega_{16 m'}, m' < 2^{c-4}
-  const StagePlan sp = make_stage_plan(c);
+  const StagePlan sp = make_stage_plan(c, true);
   ColSmem<T> S(smem_raw, sp.tl_total);
   fill_stage_consts<F>(S.K, s_rt, c);
   const uint32_t n16 = c > 4 ? 1u << (c - 4) : 1u;

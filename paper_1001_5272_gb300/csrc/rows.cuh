@@ -305,14 +305,12 @@ k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
 // Fused product rows: forward row network of A' and B', pointwise product,
 // inverse row network, result written over A'.  The inverse is left scaled
 // by 2^lr (cnet_inv2): the inverse column pass removes that factor together
-// with its own.  The last forward stage, the
-// product and the first inverse stage share one unit in registers.  Requires
-// LR >= 8 (at least two stages).  row_mul_body processes, for every row slot
-// g of the CTA, row rho_g (GA, GB: that row of A' and B' in global memory);
-// inactive slots only take part in the barriers.  A row whose positions
-// q >= bsplit lie beyond the buffers (the last row of a product transform
-// of length rounded up to a multiple of R) reads those positions from EAg /
-// EBg and writes them back to EAg.
+// with its own.  Requires LR >= 8 (at least two stages).  row_mul_body
+// processes, for every row slot g of the CTA, row rho_g (GA, GB: that row of
+// A' and B' in global memory); inactive slots only take part in the
+// barriers.  A row whose positions q >= bsplit lie beyond the buffers (the
+// last row of a product transform of length rounded up to a multiple of R)
+// reads those positions from EAg / EBg and writes them back to EAg.
 // ---------------------------------------------------------------------------
 template <class F, int LR>
 __device__ __forceinline__ void row_mul_body(
@@ -374,23 +372,34 @@ __device__ __forceinline__ void row_mul_body(
     }
     __syncthreads();
   }
-  // last forward stage (r_lo = 0, L = 4) + product + first inverse stage
+  // last forward stage (r_lo = 0, L = 4), the pointwise product and the
+  // first inverse stage.  64-bit elements: fwd_stage_ab, then each thread
+  // reads back only the 16 entries it has just written (no barrier needed)
+  // for the product and the inverse stage; reusing fwd_stage_ab keeps the
+  // kernel's code smaller, which measured faster.  32-bit elements: all
+  // three in registers on one unit (their code is smaller; measured faster).
   if (active) {
-    const T RF = S.RF[(g * 2) * 5 + last];
     const T RFi = S.RF[(g * 2 + 1) * 5 + last];
-    const T* TLs = S.TL + sp.s[last].tl_off;
     const T* TLis = S.TLi + sp.s[last].tl_off;
     const uint32_t u = (uint32_t)t;  // one unit per thread
-    T xa[16], xb[16];
+    T xa[16];
+    if constexpr (sizeof(T) == 8) {
+      fwd_stage_ab<F, 4, false>(ZA, GA, ZB, GB, 0, t, Tpr,
+                                S.RF[(g * 2) * 5 + last],
+                                S.TL + sp.s[last].tl_off, *S.K);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      xa[i] = ZA[swz(u * 16 + i)];
-      xb[i] = ZB[swz(u * 16 + i)];
-    }
-    {
-      // twist both operands with one running power (keeps register use
-      // at two units plus two words)
-      const T zeta = F::mul_tw(RF, TLs[u]);
+      for (int i = 0; i < 16; ++i)
+        xa[i] = F::mul_data(ZA[swz(u * 16 + i)], ZB[swz(u * 16 + i)]);
+    } else {
+      T xb[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        xa[i] = ZA[swz(u * 16 + i)];
+        xb[i] = ZB[swz(u * 16 + i)];
+      }
+      // twist both operands with one running power
+      const T zeta = F::mul_tw(S.RF[(g * 2) * 5 + last],
+                               (S.TL + sp.s[last].tl_off)[u]);
       T zp = zeta;
 #pragma unroll
       for (int i = 1; i < 16; ++i) {
@@ -398,11 +407,11 @@ __device__ __forceinline__ void row_mul_body(
         xb[i] = F::mul_tw(xb[i], zp);
         if (i < 15) zp = F::mul_tw(zp, zeta);
       }
-    }
-    cnet_fwd<F, 4>(xa, *S.K);
-    cnet_fwd<F, 4>(xb, *S.K);
+      cnet_fwd<F, 4>(xa, *S.K);
+      cnet_fwd<F, 4>(xb, *S.K);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) xa[i] = F::mul_data(xa[i], xb[i]);
+      for (int i = 0; i < 16; ++i) xa[i] = F::mul_data(xa[i], xb[i]);
+    }
     cnet_inv2<F, 4>(xa, *S.K);
     twist<F, 4>(xa, F::mul_tw(RFi, TLis[u]));
 #pragma unroll

@@ -44,18 +44,22 @@ struct StageDesc {
 };
 
 // Stages of a block of 2^lr positions, forward order (highest levels first):
-// the first stage takes lr mod 4 levels (or 4), then stages of 4 down to 0.
+// the first stage takes lr mod 4 levels (or 4), then stages of 4 down to 0;
+// with rem_last the stages of 4 come first and the last stage takes the
+// remainder (the column kernels: their first stage reads global memory, and
+// a wide first stage keeps more loads in flight per unit).
 struct StagePlan {
   int n;
   StageDesc s[5];
   int tl_total;
 };
 
-__host__ __device__ inline StagePlan make_stage_plan(int lr) {
+__host__ __device__ inline StagePlan make_stage_plan(int lr,
+                                                     bool rem_last = false) {
   StagePlan sp;
   sp.n = 0;
   int r = lr;
-  int first = lr % 4 ? lr % 4 : 4;
+  int first = (lr % 4 == 0 || (rem_last && lr > 4)) ? 4 : lr % 4;
   int L = first;
   int off = 0;
   while (r > 0) {
