@@ -118,7 +118,10 @@ tft_status tft_inverse(tft_ctx* ctx, void* X, uint64_t n, uint32_t k,
 
 /*
  * polymul(a, b): out = a * b mod p (Section 5; TFT of both operands,
- * pointwise product, ITFT).
+ * pointwise product, ITFT).  The transforms have length r rounded up to a
+ * multiple of the plan's row length R (any length >= r determines the
+ * product); the fewer than R positions past r live in the context's
+ * scratch.
  *   a, b   device pointers, na and nb elements (read only; may alias each
  *          other), 16-byte aligned.
  *   out    device pointer, r = na + nb - 1 elements, 16-byte aligned, must
