@@ -35,7 +35,6 @@ struct BatchLarge {
   uint32_t c;                        // columns padded to 2^c
   uint32_t pad;
   uint64_t row_base;                 // prefix of the row counts a_p + [b_p > 0]
-  uint64_t ci_base;                  // prefix of inverse column tiles
 };
 
 // Largest p with base(p) <= x over a non-decreasing prefix (binary search).
@@ -126,11 +125,22 @@ k_col_fwd_batch(const BatchLarge* __restrict__ d, uint32_t nl, int lr,
 
 // Phase 2: fused rows, all rows of all products flattened (row a_p of a
 // product with b_p > 0 reads and writes its positions past r_p in EA / EB).
+// With cache_prefix the CTA first copies the row prefix (32-bit) into the
+// shared memory after the row buffers, so that a row's product is a binary
+// search in shared memory rather than a chain of dependent global loads.
 template <class F, int LR>
 __global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
 k_row_mul_batch(const BatchLarge* __restrict__ d, uint32_t nl,
-                uint64_t total_rows, RootTable<typename F::T> rt) {
+                uint64_t total_rows, int cache_prefix,
+                RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE(2)
+  uint32_t* s_rb = reinterpret_cast<uint32_t*>(
+      smem_raw + row_smem_bytes<T>(LR, G, 2));
+  if (cache_prefix) {
+    for (uint32_t i = threadIdx.x; i < nl; i += blockDim.x)
+      s_rb[i] = (uint32_t)d[i].row_base;
+    __syncthreads();
+  }
   for (uint64_t row0 = (uint64_t)blockIdx.x * G; row0 < total_rows;
        row0 += (uint64_t)gridDim.x * G) {
     const uint64_t row = row0 + g;
@@ -143,7 +153,11 @@ k_row_mul_batch(const BatchLarge* __restrict__ d, uint32_t nl,
     const T* EB = nullptr;
     if (active) {
       const uint32_t p =
-          find_product(nl, row, [&](uint32_t i) { return d[i].row_base; });
+          cache_prefix
+              ? find_product(nl, row,
+                             [&](uint32_t i) { return (uint64_t)s_rb[i]; })
+              : find_product(nl, row,
+                             [&](uint32_t i) { return d[i].row_base; });
       rho = row - d[p].row_base;
       GA = reinterpret_cast<T*>(d[p].out) + rho * R;
       GB = reinterpret_cast<const T*>(d[p].work) + rho * R;
@@ -159,7 +173,7 @@ k_row_mul_batch(const BatchLarge* __restrict__ d, uint32_t nl,
 }
 
 // Phase 3: inverse columns, all R columns of every product, of length
-// a_p + [b_p > 0].  Task = (product, tile) through the prefix ci_base.
+// a_p + [b_p > 0].  Every product has R / C tiles: task = p (R / C) + j.
 template <class F>
 __global__ void TFT_COL_LAUNCH_BOUNDS(256, typename F::T)
 k_col_inv_batch(const BatchLarge* __restrict__ d, uint32_t nl,
@@ -172,10 +186,9 @@ k_col_inv_batch(const BatchLarge* __restrict__ d, uint32_t nl,
   const uint32_t R = 1u << lr;
   const uint32_t C = 1u << clog;
   for (uint64_t task = blockIdx.x; task < total; task += gridDim.x) {
-    const uint32_t p =
-        find_product(nl, task, [&](uint32_t i) { return d[i].ci_base; });
+    const uint32_t p = (uint32_t)(task >> (lr - clog));
     const BatchLarge q = d[p];
-    const uint32_t j = (uint32_t)(task - q.ci_base);
+    const uint32_t j = (uint32_t)(task & ((1u << (lr - clog)) - 1));
     const uint64_t r = (uint64_t)q.A * R + q.Bm;
     col_inv_tile<F>(smem_raw, s_rt, reinterpret_cast<T*>(q.out), nullptr, lr,
                     q.A + (q.Bm > 0 ? 1u : 0u), (int)q.c, clog, j * C, R, 0,

@@ -126,14 +126,14 @@ tft_status batch_describe(const PrimeInfo& pr, const BatchSchedule& S,
             [](const BatchSmall& x, const BatchSmall& y) {
               return x.na + x.nb > y.na + y.nb;
             });
-  // rows a_p (+ the full row a_p when b_p > 0), all R columns inverted
-  uint64_t rows_acc = 0, ci_acc = 0;
+  // rows a_p (+ the full row a_p when b_p > 0); all R columns inverted,
+  // R / C tiles per product
+  uint64_t rows_acc = 0;
   for (BatchLarge& q : *hl) {
     q.row_base = rows_acc;
-    q.ci_base = ci_acc;
     rows_acc += q.A + (q.Bm ? 1 : 0);
-    ci_acc += (R + C - 1) / C;
   }
+  const uint64_t ci_acc = (uint64_t)hl->size() * (R / C);
   memset(B, 0, sizeof(*B));
   B->nl = (uint32_t)hl->size();
   B->ns = (uint32_t)hs->size();

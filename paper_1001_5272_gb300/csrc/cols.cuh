@@ -75,15 +75,15 @@ __device__ __forceinline__ void col_fwd_stage(
   // rows still needed once this stage is done: < ceil(rows / 2^r_lo) 2^r_lo
   const uint32_t need = ((rows + (1u << r_lo) - 1) >> r_lo) << r_lo;
   const uint32_t units = 1u << (c - L + clog);
-#pragma unroll 1
-  for (uint32_t u = threadIdx.x; u < units; u += blockDim.x) {
+  // a unit whose block starts at or past `need` is skipped
+  auto live = [&](uint32_t u) {
+    return (((u >> clog) >> r_lo) << (r_lo + L)) < need;
+  };
+  auto load = [&](uint32_t u, T(&x)[U]) {
     const uint32_t cc = u & (C - 1);
     const uint32_t ut = u >> clog;
-    const uint32_t bstart = (ut >> r_lo) << (r_lo + L);
-    if (bstart >= need) continue;
     const uint64_t q = (uint64_t)q0 + cc;
     const bool colok = q < q_end;
-    T x[U];
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const uint32_t t = unit_pos(ut, r_lo, L, i);
@@ -94,6 +94,12 @@ __device__ __forceinline__ void col_fwd_stage(
         x[i] = Z[(tswz(t, clog) << clog) + cc];
       }
     }
+  };
+  auto compute_store = [&](uint32_t u, T(&x)[U]) {
+    const uint32_t cc = u & (C - 1);
+    const uint32_t ut = u >> clog;
+    const uint64_t q = (uint64_t)q0 + cc;
+    const bool colok = q < q_end;
     // the first stage's block index is 0: zeta = 1, no twist
     if (!FIRST) twist<F, L>(x, TLs[ut >> r_lo]);
     cnet_fwd<F, L>(x, K);
@@ -113,6 +119,13 @@ __device__ __forceinline__ void col_fwd_stage(
         Z[(tswz(t, clog) << clog) + cc] = x[i];
       }
     }
+  };
+#pragma unroll 1
+  for (uint32_t u = threadIdx.x; u < units; u += blockDim.x) {
+    if (!live(u)) continue;
+    T x[U];
+    load(u, x);
+    compute_store(u, x);
   }
 }
 

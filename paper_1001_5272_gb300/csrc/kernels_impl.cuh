@@ -651,7 +651,21 @@ struct Launch {
                                                       rt)));
       TFT_LR_DISPATCH_BATCH(B.lr, {
         using Geo = RowGeom<LR>;
-        const size_t smr = row_smem_bytes<T>(LR, Geo::G, 2);
+        // the row prefix goes to shared memory when its values fit 32 bits
+        // and the extra bytes cost no resident CTA
+        const size_t smr0 = row_smem_bytes<T>(LR, Geo::G, 2);
+        const size_t smr1 = smr0 + 4 * (size_t)B.nl;
+        int occ0 = 0, occ1 = 0;
+        const int cache =
+            B.total_rows < (1ull << 32) &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ0, k_row_mul_batch<F, LR>, Geo::THREADS, smr0) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ1, k_row_mul_batch<F, LR>, Geo::THREADS, smr1) ==
+                cudaSuccess &&
+            occ1 >= occ0 && occ1 > 0;
+        const size_t smr = cache ? smr1 : smr0;
         const uint64_t slots = (B.total_rows + Geo::G - 1) / Geo::G;
         TFT_LAUNCH(K_ROW_MUL,
                    (k_row_mul_batch<F, LR><<<persistent_grid(
@@ -659,7 +673,7 @@ struct Launch {
                                                  Geo::THREADS, smr, slots,
                                                  nsm),
                                              Geo::THREADS, smr, s>>>(
-                       d, B.nl, B.total_rows, rt)));
+                       d, B.nl, B.total_rows, cache, rt)));
       });
       if (B.ci_tiles)
         TFT_LAUNCH(K_COL_INV,

@@ -71,12 +71,21 @@ struct RowSmem {
   }
 };
 
+// Words between consecutive rows in shared memory.  With 32-bit elements
+// and rows of 2^8 (16 threads per row) a warp spans two rows; a 16-word gap
+// puts the second row's banks in the other half, so the two rows of a warp
+// never collide.
+template <class T>
+__host__ __device__ constexpr size_t row_stride(int lr) {
+  return ((size_t)1 << lr) + (sizeof(T) == 4 && lr <= 8 ? 16 : 0);
+}
+
 template <class T>
 __host__ __device__ inline size_t row_smem_bytes(int lr, int G, int nbuf) {
   const StagePlan sp = make_stage_plan(lr);
   size_t b = sizeof(StageConsts<T>) + sizeof(T) * (G * 10 + 2 * sp.tl_total);
   b = (b + 15) & ~(size_t)15;
-  return b + sizeof(T) * ((size_t)nbuf * G << lr);
+  return b + sizeof(T) * ((size_t)nbuf * G * row_stride<T>(lr));
 }
 
 template <class F>
@@ -239,7 +248,7 @@ template <class F, int LR>
 __global__ void __launch_bounds__(RowGeom<LR, 256>::THREADS, RowGeom<LR, 256>::template min_ctas<sizeof(typename F::T)>())
 k_row_fwd2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE_G(1, RowGeom<LR, 256>)
-  T* Zrow = S.Z + ((size_t)g << LR);
+  T* Zrow = S.Z + g * row_stride<T>(LR);
   for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
        rho0 += (uint64_t)gridDim.x * G) {
     const uint64_t rho = rho0 + g;
@@ -273,7 +282,7 @@ template <class F, int LR>
 __global__ void __launch_bounds__(RowGeom<LR, 256>::THREADS, RowGeom<LR, 256>::template min_ctas<sizeof(typename F::T)>())
 k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE_G(1, RowGeom<LR, 256>)
-  T* Zrow = S.Z + ((size_t)g << LR);
+  T* Zrow = S.Z + g * row_stride<T>(LR);
   for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
        rho0 += (uint64_t)gridDim.x * G) {
     const uint64_t rho = rho0 + g;
@@ -325,8 +334,8 @@ __device__ __forceinline__ void row_mul_body(
   constexpr int Tpr = Geo::TPR;
   constexpr int G = Geo::G;
   static_assert(Geo::NST >= 2, "fused row pass needs two stages");
-  T* ZA = S.Z + ((size_t)g << LR);
-  T* ZB = S.Z + ((size_t)(G + g) << LR);
+  T* ZA = S.Z + g * row_stride<T>(LR);
+  T* ZB = S.Z + (G + g) * row_stride<T>(LR);
   constexpr int last = Geo::NST - 1;  // r_lo = 0, L = 4
   if (active) row_factors<F>(S, sp, LR, g, t, rho, s_rt);
   __syncthreads();
@@ -479,8 +488,8 @@ __device__ __forceinline__ void row_last_body(
   constexpr uint32_t R = Geo::R;
   constexpr int Tpr = Geo::TPR;
   constexpr int G = Geo::G;
-  T* ZA = S.Z + ((size_t)g << LR);
-  T* ZB = S.Z + ((size_t)(G + g) << LR);
+  T* ZA = S.Z + g * row_stride<T>(LR);
+  T* ZB = S.Z + (G + g) * row_stride<T>(LR);
   constexpr int last = Geo::NST - 1;
   if (active) row_factors<F>(S, sp, LR, g, t, rho, s_rt);
   if (active) {

@@ -43,11 +43,14 @@ struct StageDesc {
   int tl_off;  // offset of this stage's local twist table (2^{lr-r_lo-L})
 };
 
-// Stages of a block of 2^lr positions, forward order (highest levels first):
-// the first stage takes lr mod 4 levels (or 4), then stages of 4 down to 0;
-// with rem_last the stages of 4 come first and the last stage takes the
-// remainder (the column kernels: their first stage reads global memory, and
-// a wide first stage keeps more loads in flight per unit).
+// Stages of a block of 2^lr positions, forward order (highest levels first).
+// Rows: the first stage takes lr mod 4 levels (or 4), then stages of 4 down
+// to 0.  Columns (balanced): the fewest stages, ceil(c / 4), with the levels
+// spread as evenly as possible and the wider stages first -- the first
+// stage reads global memory, and a wide one keeps more loads in flight per
+// unit, while no stage is left with one or two levels when three fit (a
+// narrow stage pays a shared-memory round trip and a unit's overhead for
+// few butterflies).
 struct StagePlan {
   int n;
   StageDesc s[5];
@@ -55,14 +58,18 @@ struct StagePlan {
 };
 
 __host__ __device__ inline StagePlan make_stage_plan(int lr,
-                                                     bool rem_last = false) {
+                                                     bool balanced = false) {
   StagePlan sp;
   sp.n = 0;
+  const int nst = (lr + 3) / 4;
   int r = lr;
-  int first = (lr % 4 == 0 || (rem_last && lr > 4)) ? 4 : lr % 4;
-  int L = first;
   int off = 0;
-  while (r > 0) {
+  for (int i = 0; r > 0; ++i) {
+    int L;
+    if (balanced)
+      L = lr / nst + (i < lr % nst ? 1 : 0);
+    else
+      L = i == 0 ? (lr % 4 ? lr % 4 : 4) : 4;
     if (L > r) L = r;
     sp.s[sp.n].r_lo = r - L;
     sp.s[sp.n].L = L;
@@ -70,7 +77,6 @@ __host__ __device__ inline StagePlan make_stage_plan(int lr,
     off += 1 << (lr - (r - L) - L);  // entries: 2^{lr - r_lo - L}
     ++sp.n;
     r -= L;
-    L = 4;
   }
   sp.tl_total = off;
   return sp;
