@@ -290,7 +290,17 @@ k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
     T* Grow = X + rho * R;
     if (active) {
       row_factors<F>(S, sp, LR, g, t, rho, s_rt);
-      for (uint32_t q = t; q < R; q += Tpr) Zrow[swz(q)] = Grow[q];
+      // eight loads in flight per thread
+      constexpr uint32_t NQ = R / Tpr;
+      static_assert(NQ % 8 == 0, "row load batches of eight");
+#pragma unroll
+      for (uint32_t k0 = 0; k0 < NQ; k0 += 8) {
+        T v[8];
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) v[k] = Grow[t + (k0 + k) * Tpr];
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) Zrow[swz(t + (k0 + k) * Tpr)] = v[k];
+      }
     }
     __syncthreads();
 #pragma unroll 1
@@ -339,9 +349,6 @@ __device__ __forceinline__ void row_mul_body(
   constexpr int last = Geo::NST - 1;  // r_lo = 0, L = 4
   if (active) row_factors<F>(S, sp, LR, g, t, rho, s_rt);
   __syncthreads();
-  // both rows to shared memory (coalesced), then the first stage from
-  // there: reading the first stage straight from global memory lets the
-  // scheduler overlap the two operands' loads and spill registers
   // the split is needed again by the last stage: parked in shared memory
   // so that it holds no registers across the stages
   __shared__ uint32_t s_bsplit[G];
@@ -350,7 +357,13 @@ __device__ __forceinline__ void row_mul_body(
     s_bsplit[g] = bsplit;
     s_ealt[g] = EAg;
   }
-  if (active) {
+  // both rows to shared memory (coalesced), then the first stage from
+  // there: reading the first stage straight from global memory lets the
+  // scheduler overlap the two operands' loads and spill registers.  32-bit
+  // elements: eight positions of each operand in flight per thread (measured
+  // faster there, and slower for 64-bit elements, whose registers are
+  // scarcer)
+  if (active && sizeof(T) == 8) {
     if (bsplit >= R) {
       for (uint32_t q = t; q < R; q += Tpr) {
         ZA[swz(q)] = GA[q];
@@ -360,6 +373,26 @@ __device__ __forceinline__ void row_mul_body(
       for (uint32_t q = t; q < R; q += Tpr) {
         ZA[swz(q)] = q < bsplit ? GA[q] : EAg[q];
         ZB[swz(q)] = q < bsplit ? GB[q] : EBg[q];
+      }
+    }
+  } else if (active) {
+    constexpr uint32_t NQ = R / Tpr;  // positions per thread
+    static_assert(NQ % 8 == 0, "row load batches of eight");
+#pragma unroll
+    for (uint32_t k0 = 0; k0 < NQ; k0 += 8) {
+      T va[8], vb[8];
+#pragma unroll
+      for (uint32_t k = 0; k < 8; ++k) {
+        const uint32_t q = t + (k0 + k) * Tpr;
+        const bool mem = q < bsplit;  // bsplit >= R for a full row
+        va[k] = mem ? GA[q] : EAg[q];
+        vb[k] = mem ? GB[q] : EBg[q];
+      }
+#pragma unroll
+      for (uint32_t k = 0; k < 8; ++k) {
+        const uint32_t q = t + (k0 + k) * Tpr;
+        ZA[swz(q)] = va[k];
+        ZB[swz(q)] = vb[k];
       }
     }
   }

@@ -120,6 +120,23 @@ def test_batch_schedules(ctxs, pr, params):
         assert np.array_equal(c, NV.tft_polymul(pr, a, b)), (pairs[i], params)
 
 
+@pytest.mark.parametrize("pr", PRIMES, ids=lambda p: p.name)
+def test_batch_rounded_length_edges(ctxs, pr):
+    # one batch on rows of 2^8 whose large products have r = a 2^8 + b with
+    # b = 0, 1, 128, 255 and a + 1 a power of two, just above one, or odd
+    # (a product with b > 0 runs its transforms at length (a + 1) 2^8)
+    pairs = []
+    for a_rows in (31, 32, 63, 64, 155):
+        for b_len in (0, 1, 128, 255):
+            r = a_rows * 256 + b_len
+            na = r // 2 + 1
+            pairs.append((na, r - na + 1))
+    params = {"lr": 8, "small_log": 9, "clog": 3}
+    A, B, C = run_batch(ctxs[pr.name], pr, pairs, params, seed=4)
+    for i, (a, b, c) in enumerate(zip(A, B, C)):
+        assert np.array_equal(c, NV.tft_polymul(pr, a, b)), pairs[i]
+
+
 def test_batch_only_small_and_only_large(ctxs):
     pr = F.P998244353
     ctx = ctxs[pr.name]

@@ -181,6 +181,34 @@ def test_polymul_two_pass_sizes(ctxs, pr):
         assert np.array_equal(gpu_polymul(ctxs, pr, a, b), ref), (na, nb)
 
 
+@pytest.mark.parametrize("pr", PRIMES, ids=lambda p: p.name)
+def test_polymul_rounded_length_edges(ctxs, pr):
+    # the product's transforms run at length (a + 1) R when r = a R + b with
+    # b > 0 (the R - b positions past r in the context's scratch).  Edges: b
+    # = 0, 1, R/2 and R - 1; a + 1 a power of two (each column's inverse is
+    # a full network), just above one, and odd
+    tft = _lib()
+    cases = []
+    for lr, a_vals in ((8, (127, 128, 155)), (9, (255, 256, 301))):
+        R = 1 << lr
+        for a_rows in a_vals:
+            for b_len in (0, 1, R // 2, R - 1):
+                r = a_rows * R + b_len
+                P = tft.tft_describe_plan(pr.name, r)
+                if P["small"] or P["lr"] != lr:
+                    continue
+                assert (P["a"], P["b"]) == (a_rows, b_len)
+                cases.append(r)
+    assert len(cases) >= 12
+    for r in cases:
+        na = r // 3 + 1
+        nb = r - na + 1
+        a = rand(pr, na, r)
+        b = rand(pr, nb, r + 1)
+        assert np.array_equal(gpu_polymul(ctxs, pr, a, b),
+                              NV.tft_polymul(pr, a, b)), r
+
+
 def test_polymul_aliased_operands(ctxs):
     # a and b may be the same buffer (squaring)
     tft = _lib()
