@@ -317,8 +317,7 @@ struct Launch {
     if ((e = set_smem<F>((const void*)k_row_fwd2<F, LRV>, mx))) return e;  \
     if ((e = set_smem<F>((const void*)k_row_inv2<F, LRV>, mx))) return e;  \
     if ((e = set_smem<F>((const void*)k_row_mul2<F, LRV>, mx))) return e;  \
-    if ((e = set_smem<F>((const void*)k_row_last2<F, LRV, false>, mx)))    \
-      return e;                                                            \
+    if ((e = set_smem<F>((const void*)k_row_last2<F, LRV>, mx))) return e; \
   } while (0)
 
   static cudaError_t prepare(size_t mx) {
@@ -463,12 +462,9 @@ struct Launch {
       TFT_LR_DISPATCH(P.lr, {
         using Geo = RowGeom<LR>;
         TFT_LAUNCH_ON(K_LASTROW_FWD, s2,
-                      (k_row_last2<F, LR, false><<<1, Geo::THREADS,
-                                                   row_smem_bytes<T>(LR, Geo::G,
-                                                                     1),
-                                                   s2>>>(x, E, nullptr,
-                                                         nullptr, P.a, P.b,
-                                                         rt)));
+                      (k_row_last2<F, LR><<<1, Geo::THREADS,
+                                            row_smem_bytes<T>(LR, Geo::G, 1),
+                                            s2>>>(x, E, P.a, P.b, rt)));
       });
     }
     cudaError_t e = rows_fwd_v2(x, P, rt, nsm, s, H);

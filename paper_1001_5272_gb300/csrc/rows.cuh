@@ -504,32 +504,25 @@ k_row_mul2(typename F::T* out, const typename F::T* __restrict__ work,
 }
 
 // ---------------------------------------------------------------------------
-// The ragged last row (block a, first b outputs) on the stage engine: the
-// full forward network of block a, whose inputs are the long columns' last
-// entries (q < b, in the buffer) and E_q (q >= b, scratch).  TWO: product
-// (both operands, then the pointwise product); else a forward transform.
-// Only outputs q < b are stored, over the row's first b words.
+// The ragged last row of a forward transform (block a, first b outputs) on
+// the stage engine: the full forward network of block a, whose inputs are
+// the long columns' last entries (q < b, in the buffer) and E_q (q >= b,
+// scratch).  Only outputs q < b are stored, over the row's first b words.
+// (Products run their transforms at a length that has no ragged row.)
 // ---------------------------------------------------------------------------
-template <class F, int LR, bool TWO>
-__device__ __forceinline__ void row_last_body(
-    RowSmem<typename F::T>& S, const StagePlan& sp, int g, int t,
-    bool active, uint64_t rho, uint32_t b, typename F::T* GA,
-    const typename F::T* EA, const typename F::T* GB,
-    const typename F::T* EB, const RootTable<typename F::T>& s_rt) {
-  using T = typename F::T;
-  using Geo = RowGeom<LR>;
-  constexpr uint32_t R = Geo::R;
-  constexpr int Tpr = Geo::TPR;
-  constexpr int G = Geo::G;
+template <class F, int LR>
+__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
+k_row_last2(typename F::T* X, const typename F::T* __restrict__ E,
+            uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
+  TFT_ROW_PROLOGUE(1)
+  // one row: slot 0 of the first CTA
+  const bool active = blockIdx.x == 0 && g == 0;
+  T* GA = X + a * R;
   T* ZA = S.Z + g * row_stride<T>(LR);
-  T* ZB = S.Z + (G + g) * row_stride<T>(LR);
   constexpr int last = Geo::NST - 1;
-  if (active) row_factors<F>(S, sp, LR, g, t, rho, s_rt);
   if (active) {
-    for (uint32_t q = t; q < R; q += Tpr) {
-      ZA[swz(q)] = q < b ? GA[q] : EA[q];
-      if (TWO) ZB[swz(q)] = q < b ? GB[q] : EB[q];
-    }
+    row_factors<F>(S, sp, LR, g, t, a, s_rt);
+    for (uint32_t q = t; q < R; q += Tpr) ZA[swz(q)] = q < b ? GA[q] : E[q];
   }
   __syncthreads();
 #pragma unroll 1
@@ -538,19 +531,10 @@ __device__ __forceinline__ void row_last_body(
       const T RF = S.RF[(g * 2) * 5 + si];
       const T* TLs = S.TL + sp.s[si].tl_off;
       const int r_lo = Geo::r_lo(si);
-      if (si == 0) {
-        if (TWO)
-          fwd_stage_ab<F, Geo::L0, false>(ZA, GA, ZB, GB, r_lo, t, Tpr, RF,
-                                          TLs, *S.K);
-        else
-          fwd_stage<F, Geo::L0, false>(ZA, GA, r_lo, t, Tpr, RF, TLs, *S.K);
-      } else {
-        if (TWO)
-          fwd_stage_ab<F, 4, false>(ZA, GA, ZB, GB, r_lo, t, Tpr, RF, TLs,
-                                    *S.K);
-        else
-          fwd_stage<F, 4, false>(ZA, GA, r_lo, t, Tpr, RF, TLs, *S.K);
-      }
+      if (si == 0)
+        fwd_stage<F, Geo::L0, false>(ZA, GA, r_lo, t, Tpr, RF, TLs, *S.K);
+      else
+        fwd_stage<F, 4, false>(ZA, GA, r_lo, t, Tpr, RF, TLs, *S.K);
     }
     __syncthreads();
   }
@@ -561,36 +545,12 @@ __device__ __forceinline__ void row_last_body(
     T xa[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) xa[i] = ZA[swz(u * 16 + i)];
-    const T zeta = F::mul_tw(RF, TLs[u]);
-    twist<F, 4>(xa, zeta);
+    twist<F, 4>(xa, F::mul_tw(RF, TLs[u]));
     cnet_fwd<F, 4>(xa, *S.K);
-    if (TWO) {
-      T xb[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) xb[i] = ZB[swz(u * 16 + i)];
-      twist<F, 4>(xb, zeta);
-      cnet_fwd<F, 4>(xb, *S.K);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) xa[i] = F::mul_data(xa[i], xb[i]);
-    }
 #pragma unroll
     for (int i = 0; i < 16; ++i)
       if (u * 16 + i < b) GA[u * 16 + i] = F::canon(xa[i]);
   }
-  __syncthreads();
-}
-
-// Last row of one transform (TWO = false) or product (TWO = true).
-template <class F, int LR, bool TWO>
-__global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
-k_row_last2(typename F::T* X, const typename F::T* __restrict__ E,
-            const typename F::T* work, const typename F::T* __restrict__ EB,
-            uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
-  TFT_ROW_PROLOGUE(TWO ? 2 : 1)
-  // one row: slot 0 of the first CTA
-  row_last_body<F, LR, TWO>(S, sp, g, t, blockIdx.x == 0 && g == 0, a,
-                            (uint32_t)b, X + a * R, E,
-                            TWO ? work + a * R : nullptr, EB, s_rt);
 }
 
 // Dispatch a runtime lr in [8, 12] (the batched large class) to LR.
