@@ -126,6 +126,19 @@ tft_status batch_describe(const PrimeInfo& pr, const BatchSchedule& S,
             [](const BatchSmall& x, const BatchSmall& y) {
               return x.na + x.nb > y.na + y.nb;
             });
+  // large products by column height, so that the column passes can run the
+  // shorter columns in smaller tiles (more resident CTAs) than the tallest
+  std::stable_sort(hl->begin(), hl->end(),
+                   [](const BatchLarge& x, const BatchLarge& y) {
+                     return x.c < y.c;
+                   });
+  uint32_t nl_lo = 0;
+  int cmax_lo = 0;
+  for (const BatchLarge& q : *hl)
+    if ((int)q.c < cmax) {
+      ++nl_lo;
+      cmax_lo = std::max(cmax_lo, (int)q.c);
+    }
   // rows a_p (+ the full row a_p when b_p > 0); all R columns inverted,
   // R / C tiles per product
   uint64_t rows_acc = 0;
@@ -141,6 +154,8 @@ tft_status batch_describe(const PrimeInfo& pr, const BatchSchedule& S,
   B->lr = S.lr;
   B->clog = S.clog;
   B->cmax = cmax;
+  B->nl_lo = nl_lo;
+  B->cmax_lo = cmax_lo;
   B->total_rows = rows_acc;
   B->ci_tiles = ci_acc;
   return TFT_OK;

@@ -74,6 +74,8 @@ struct BatchLaunch {
   int lr;              // row length of the large class
   int clog;            // columns per tile
   int cmax;            // largest column log length
+  uint32_t nl_lo;      // large products (first, sorted by c) with c < cmax
+  int cmax_lo;         // their largest column log length
   uint64_t total_rows; // sum of a_p + [b_p > 0]
   uint64_t ci_tiles;   // inverse column tiles
 };
