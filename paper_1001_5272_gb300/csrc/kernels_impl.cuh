@@ -20,7 +20,11 @@
 // columns (ITFT of length a) and E_q by Horner; the last row by the
 // generalized block inverse with known inputs E_q at q >= b; inverse long
 // columns (length a + 1).  Global memory holds the n-word buffer plus the
-// R-word scratch; every transform works in shared memory.
+// R-word scratch; every transform works in shared memory.  The product on
+// rows of at least 2^8 runs its transforms at length (a + 1) R instead (any
+// length >= r determines the product), so it has no ragged row: every
+// column has length a + 1 and row a is a full row whose positions past r
+// live in the R-word scratch (Launch::polymul).
 #pragma once
 #include <cuda_runtime.h>
 
