@@ -179,8 +179,9 @@ tft_status tft_restricted_schedule(uint64_t r, uint64_t* q, uint64_t* L,
  *
  * Products with r = na + nb - 1 <= 2^small_log run one per CTA entirely in
  * shared memory; the others use the row/column split with one row length
- * 2^lr for all of them, as three launches that each cover every large
- * product (forward columns, fused rows, inverse columns).  Each launch is
+ * 2^lr for all of them, in three phases that each cover every large
+ * product (forward columns, fused rows, inverse columns; a column phase is
+ * two launches when the shorter columns fit smaller tiles).  Each launch is
  * persistent over its task list.
  *
  * Usage: tft_ctx_reserve_batch once (reserves the descriptor tables for up
