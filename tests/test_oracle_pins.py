@@ -352,6 +352,42 @@ def test_tft_polymul_random_sizes(pr):
 
 
 @pytest.mark.parametrize("pr", PRIMES, ids=lambda p: p.name)
+def test_product_through_any_longer_tft_length(pr):
+    # Section 1.2: a polynomial of degree < n' is determined by its TFT of
+    # length n' (the transform is invertible), so the product of degree < r
+    # comes out of transforms of any length n' >= r -- the GPU product runs
+    # them at r rounded up to a multiple of its row length.  The inverse of
+    # the pointwise product returns the r product coefficients followed by
+    # n' - r zeros; a length below r loses information.
+    rng = np.random.default_rng(37)
+    for na, nb in ((5, 9), (100, 157), (300, 4), (513, 512)):
+        a = rng.integers(0, pr.p, na, dtype=np.uint64)
+        b = rng.integers(0, pr.p, nb, dtype=np.uint64)
+        r = na + nb - 1
+        want = [int(v) for v in NV.schoolbook(pr, a, b)]
+        for n2 in sorted({r, r + 1, r + 37, -(-r // 64) * 64,
+                          1 << (r - 1).bit_length()}):
+            A = NV.alg1_tft(pr, np.concatenate(
+                [a, np.zeros(n2 - na, dtype=np.uint64)]))
+            B = NV.alg1_tft(pr, np.concatenate(
+                [b, np.zeros(n2 - nb, dtype=np.uint64)]))
+            Cp = np.array([int(x) * int(y) % pr.p for x, y in zip(A, B)],
+                          dtype=np.uint64)
+            c = [int(v) for v in NV.alg2_itft(pr, Cp)]
+            assert c[:r] == want and c[r:] == [0] * (n2 - r), (na, nb, n2)
+        # one position short of r: the top coefficient is lost
+        n2 = r - 1
+        if n2 >= max(na, nb):
+            A = NV.alg1_tft(pr, np.concatenate(
+                [a, np.zeros(n2 - na, dtype=np.uint64)]))
+            B = NV.alg1_tft(pr, np.concatenate(
+                [b, np.zeros(n2 - nb, dtype=np.uint64)]))
+            Cp = np.array([int(x) * int(y) % pr.p for x, y in zip(A, B)],
+                          dtype=np.uint64)
+            assert [int(v) for v in NV.alg2_itft(pr, Cp)] != want[:n2]
+
+
+@pytest.mark.parametrize("pr", PRIMES, ids=lambda p: p.name)
 def test_polymul_random_point_large(pr):
     # Schwartz-Zippel: C(z) = A(z) B(z) at random z, independent of the TFT.
     rng = np.random.default_rng(41)
