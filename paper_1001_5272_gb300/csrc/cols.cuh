@@ -62,8 +62,11 @@ __host__ __device__ inline size_t col_smem_bytes(int c, int clog) {
 
 // One forward stage over all units of a column tile.  FIRST: inputs from
 // global memory (positions >= n_src and rows >= rows are zero); LAST: outputs
-// to global memory (rows t < a to dst, row a to dst or E).
-template <class F, int L, bool FIRST, bool LAST>
+// to global memory (rows t < a to dst, row a to dst or E).  TZ (first stage
+// only): the operand has no entries in the upper half of the padded column
+// (rows >= 2^{c-1}), so the stage's top level is a copy and those inputs are
+// not loaded.
+template <class F, int L, bool FIRST, bool LAST, bool TZ = false>
 __device__ __forceinline__ void col_fwd_stage(
     typename F::T* Z, const typename F::T* src, uint64_t n_src,
     typename F::T* dst, typename F::T* E, uint64_t R, uint64_t a, uint64_t b,
@@ -89,7 +92,9 @@ __device__ __forceinline__ void col_fwd_stage(
       const uint32_t t = unit_pos(ut, r_lo, L, i);
       if (FIRST) {
         const uint64_t pos = q + (uint64_t)t * R;
-        x[i] = (colok && t < rows && pos < n_src) ? src[pos] : T(0);
+        x[i] = (!(TZ && i >= U / 2) && colok && t < rows && pos < n_src)
+                   ? src[pos]
+                   : T(0);
       } else {
         x[i] = Z[(tswz(t, clog) << clog) + cc];
       }
@@ -102,7 +107,7 @@ __device__ __forceinline__ void col_fwd_stage(
     const bool colok = q < q_end;
     // the first stage's block index is 0: zeta = 1, no twist
     if (!FIRST) twist<F, L>(x, TLs[ut >> r_lo]);
-    cnet_fwd<F, L>(x, K);
+    cnet_fwd<F, L, FIRST && TZ>(x, K);
 #pragma unroll
     for (int i = 0; i < U; ++i) {
       const uint32_t t = unit_pos(ut, r_lo, L, i);
@@ -153,23 +158,34 @@ __device__ void col_fwd_tile(unsigned char* smem_raw,
   __syncthreads();
   const uint64_t R = 1ull << lr;
   const uint32_t rows = (uint32_t)(a + (b > 0 ? 1 : 0));
+  // the operand's rows (the longest column's) all below 2^{c-1}: the top
+  // level is a copy (the first stage covers it)
+  const bool tz = c >= 1 && ((n_src + R - 1) >> lr) <= (1ull << (c - 1));
   for (int si = 0; si < sp.n; ++si) {
     const int r_lo = sp.s[si].r_lo;
     const T* TLs = S.TL + sp.s[si].tl_off;
     const bool first = si == 0, last = si == sp.n - 1;
-#define TFT_COL_FWD_CALL(FI, LA)                                            \
+#define TFT_COL_FWD_CALL(FI, LA, TZ)                                        \
   TFT_STAGE_SWITCH(sp.s[si].L,                                              \
-                   (col_fwd_stage<F, LL, FI, LA>(S.Z, src, n_src, dst, E, R, \
-                                                 a, b, rows, c, clog, q0,   \
-                                                 q_end, r_lo, TLs, *S.K)))
+                   (col_fwd_stage<F, LL, FI, LA, TZ>(                       \
+                       S.Z, src, n_src, dst, E, R, a, b, rows, c, clog, q0, \
+                       q_end, r_lo, TLs, *S.K)))
     if (first && last) {
-      TFT_COL_FWD_CALL(true, true);
+      if (tz) {
+        TFT_COL_FWD_CALL(true, true, true);
+      } else {
+        TFT_COL_FWD_CALL(true, true, false);
+      }
     } else if (first) {
-      TFT_COL_FWD_CALL(true, false);
+      if (tz) {
+        TFT_COL_FWD_CALL(true, false, true);
+      } else {
+        TFT_COL_FWD_CALL(true, false, false);
+      }
     } else if (last) {
-      TFT_COL_FWD_CALL(false, true);
+      TFT_COL_FWD_CALL(false, true, false);
     } else {
-      TFT_COL_FWD_CALL(false, false);
+      TFT_COL_FWD_CALL(false, false, false);
     }
 #undef TFT_COL_FWD_CALL
     __syncthreads();

@@ -169,7 +169,9 @@ __device__ __forceinline__ void powers(typename F::T (&pw)[1 << L],
                     : F::mul_tw(pw[i / 2], pw[i / 2]);
 }
 
-template <class F, int L>
+// TOPCOPY: the upper half of the unit's inputs is known to be zero, so the
+// top level's butterflies (u, 0) -> (u, u) are copies.
+template <class F, int L, bool TOPCOPY = false>
 __device__ __forceinline__ void cnet_fwd(typename F::T (&x)[1 << L],
                                          const StageConsts<typename F::T>& K) {
   using T = typename F::T;
@@ -178,6 +180,10 @@ __device__ __forceinline__ void cnet_fwd(typename F::T (&x)[1 << L],
 #pragma unroll
     for (int i = 0; i < (1 << L); ++i) {
       if (i & (1 << d)) continue;
+      if (TOPCOPY && d == L - 1) {
+        x[i + (1 << d)] = x[i];
+        continue;
+      }
       const int k = i >> (d + 1);
       const T w = x[i + (1 << d)];
       const T m = k == 0 ? w : F::mul_tw(w, K.c[k]);
