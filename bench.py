@@ -54,9 +54,9 @@ MUL32_PER_MODMUL_GOLD = 4
 # DRAM bytes (read + write) per launch of the product's kernels, from one ncu
 # capture of this workload's product (dram__bytes_read.sum +
 # dram__bytes_write.sum); to be re-taken whenever the kernel changes.
-NCU_TRAFFIC = {"k_row_mul": 128423424 + 49781760,
-               "k_col_fwd": (43044096 + 34707712 + 26976768 + 27755776) / 2,
-               "k_col_inv": 64156672 + 16331776}
+NCU_TRAFFIC = {"k_row_mul": 128531712 + 50144512,
+               "k_col_fwd": (43047168 + 33781760 + 26969856 + 27250176) / 2,
+               "k_col_inv": 64190976 + 16820480}
 NCU_TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
                       "on k_row_mul2 / k_col_fwd2 / k_col_inv2, this workload")
 # algorithmic bytes per launch: the row pass reads A' and B' and writes C'
