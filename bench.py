@@ -440,6 +440,30 @@ def run_ours(args):
             "polymul_footprint": {"device_bytes_inplace": pin_b,
                                   "device_bytes_padded": ppad_b},
         }
+        # ---- the same transforms without global scratch -------------------
+        x0 = x.clone()
+        zf, zi = [], []
+        for _ in range(2):
+            tft.tft_forward_noscratch(2, x, 25)
+            tft.tft_inverse_noscratch(2, x, 25)
+        for _ in range(max(3, steps // 2)):
+            flush.zero_()
+            ev[0].record(stream)
+            tft.tft_forward_noscratch(2, x, 25, stream)
+            ev[1].record(stream)
+            flush.zero_()
+            ev[2].record(stream)
+            tft.tft_inverse_noscratch(2, x, 25, stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            zf.append(ev[0].elapsed_time(ev[1]))
+            zi.append(ev[2].elapsed_time(ev[3]))
+        extra["tft_n17838137_noscratch"] = {
+            "forward_ms": statistics.median(zf),
+            "inverse_ms": statistics.median(zi),
+            "device_bytes_beyond_x": 0,
+            "roundtrip_identity": bool(torch.equal(x, x0))}
+        del x0
         # ---- the space-restricted product (Algorithm 3) -------------------
         out_r = torch.empty(R_PROD, dtype=torch.int64, device=dev)
         for _ in range(2):

@@ -364,6 +364,31 @@ tft_status tft_forward_noalloc(tft_prime prime, void* x, uint64_t n,
                                uint32_t k, void* stream);
 
 /*
+ * tft_forward_noscratch / tft_inverse_noscratch: the in-place forward and
+ * inverse TFT of tft_forward and tft_inverse (the same results, bit for
+ * bit) reading and writing no device memory but the n-word buffer x: no
+ * context, no scratch array, no allocation (Propositions 3.2 and 4.2 bound
+ * the paper's own auxiliary space by O(1) cells).  The other transforms keep
+ * the ragged last row's inputs E_q = C_q(omega_a) of the short columns in an
+ * R-word scratch; here one cluster of 8 CTAs evaluates them by Horner's rule
+ * straight from the buffer (the raw short columns before the forward
+ * transforms them, the recovered ones after the inverse has) and runs the
+ * last row from its shared memory -- extra work of about one multiply per
+ * coefficient of the short columns, and a serial step between the column
+ * launches.
+ *   x, n, k, stream  as in tft_forward (x a 16-byte aligned device pointer
+ *                    on the calling thread's current device).
+ * Errors: as tft_forward, without the context's max_len (n up to 2^25 for
+ * 2^64 - 2^32 + 1, min(2^K, 2^27) otherwise).  The first call on a device
+ * configures the kernels for it (no allocation); make it before capturing
+ * any stream on that device.  Calls may overlap freely (no shared state).
+ */
+tft_status tft_forward_noscratch(tft_prime prime, void* x, uint64_t n,
+                                 uint32_t k, void* stream);
+tft_status tft_inverse_noscratch(tft_prime prime, void* x, uint64_t n,
+                                 uint32_t k, void* stream);
+
+/*
  * Host-buffer variants: the same operations on HOST buffers.  Each call
  * copies the inputs to the context's staging buffers (cudaMemcpyAsync on
  * `stream`), runs the transform or product there, copies the result back and

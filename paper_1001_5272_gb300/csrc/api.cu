@@ -325,6 +325,48 @@ tft_status tft_forward_noalloc(tft_prime prime, void* x, uint64_t n,
   return TFT_OK;
 }
 
+static tft_status noscratch_transform(tft_prime prime, void* x, uint64_t n,
+                                      uint32_t k, void* stream, bool inv) {
+  if (!valid_prime((int)prime) || !x || n == 0) return TFT_EINVAL;
+  const PrimeInfo& pr = kPrimes[(int)prime];
+  if ((int)k > pr.K || (k < 64 && n > (1ull << k))) return TFT_EINVAL;
+  if (!aligned16(x)) return TFT_EINVAL;
+  Plan P;
+  if (!make_plan((int)prime, n, &P)) return TFT_ERANGE;
+  int dev = -1;
+  if (note(cudaGetDevice(&dev)) != cudaSuccess) return TFT_ECUDA;
+  NoallocDevice* d = nullptr;
+  tft_status st = noalloc_setup((int)prime, dev, &d);
+  if (st != TFT_OK) return st;
+  // The root table is built on the stack; nothing is allocated and no
+  // device memory but x is read or written.
+  tft_ctx tmp;
+  memset(&tmp, 0, sizeof(tmp));
+  tmp.pr = pr;
+  build_root_table(&tmp);
+  const uint64_t wa = P.small ? 0 : to_tw(pr, omega_s(pr, P.a));
+  cudaError_t e =
+      inv ? launch_inverse_zs((int)prime, x, n, P, wa, tmp.rt, d->nsm,
+                              (cudaStream_t)stream, nullptr)
+          : launch_forward_zs((int)prime, x, n, P, wa, tmp.rt, d->nsm,
+                              (cudaStream_t)stream, nullptr);
+  if (e != cudaSuccess) {
+    note(e);
+    return TFT_ECUDA;
+  }
+  return TFT_OK;
+}
+
+tft_status tft_forward_noscratch(tft_prime prime, void* x, uint64_t n,
+                                 uint32_t k, void* stream) {
+  return noscratch_transform(prime, x, n, k, stream, false);
+}
+
+tft_status tft_inverse_noscratch(tft_prime prime, void* x, uint64_t n,
+                                 uint32_t k, void* stream) {
+  return noscratch_transform(prime, x, n, k, stream, true);
+}
+
 tft_status tft_ctx_create(tft_prime prime, int device, uint64_t max_len,
                           uint32_t flags, tft_ctx** out) {
   if (!out) return TFT_EINVAL;

@@ -18,6 +18,12 @@ namespace tftgb {
                              cudaStream_t s, const LaunchHook* hook,          \
                              const AuxStreams* aux);                          \
   PlanSmem NAME##_plan_smem(const Plan& P);                                   \
+  cudaError_t NAME##_forward_zs(void* x, uint64_t n, const Plan& P,           \
+                                uint64_t omega_a_tw, const void* rt, int nsm, \
+                                cudaStream_t s, const LaunchHook* hook);      \
+  cudaError_t NAME##_inverse_zs(void* x, uint64_t n, const Plan& P,           \
+                                uint64_t omega_a_tw, const void* rt, int nsm, \
+                                cudaStream_t s, const LaunchHook* hook);      \
   cudaError_t NAME##_batch(const BatchLaunch& B, const void* rt, int nsm,   \
                            cudaStream_t s, const LaunchHook* hook,          \
                            const AuxStreams* aux);                          \
@@ -69,6 +75,22 @@ cudaError_t launch_inverse(int prime, void* x, uint64_t n, const Plan& P,
   TFT_BY_PRIME(prime, p998_inverse(x, n, P, E, omega_a_tw, rt, nsm, s, hook),
                p2013_inverse(x, n, P, E, omega_a_tw, rt, nsm, s, hook),
                gold_inverse(x, n, P, E, omega_a_tw, rt, nsm, s, hook));
+}
+
+cudaError_t launch_forward_zs(int prime, void* x, uint64_t n, const Plan& P,
+                              uint64_t omega_a_tw, const void* rt, int nsm,
+                              cudaStream_t s, const LaunchHook* hook) {
+  TFT_BY_PRIME(prime, p998_forward_zs(x, n, P, omega_a_tw, rt, nsm, s, hook),
+               p2013_forward_zs(x, n, P, omega_a_tw, rt, nsm, s, hook),
+               gold_forward_zs(x, n, P, omega_a_tw, rt, nsm, s, hook));
+}
+
+cudaError_t launch_inverse_zs(int prime, void* x, uint64_t n, const Plan& P,
+                              uint64_t omega_a_tw, const void* rt, int nsm,
+                              cudaStream_t s, const LaunchHook* hook) {
+  TFT_BY_PRIME(prime, p998_inverse_zs(x, n, P, omega_a_tw, rt, nsm, s, hook),
+               p2013_inverse_zs(x, n, P, omega_a_tw, rt, nsm, s, hook),
+               gold_inverse_zs(x, n, P, omega_a_tw, rt, nsm, s, hook));
 }
 
 cudaError_t launch_polymul(int prime, const void* a, uint64_t na,

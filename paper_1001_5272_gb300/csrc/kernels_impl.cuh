@@ -32,6 +32,7 @@
 #include "alg3.cuh"
 #include "batch.cuh"
 #include "cols.cuh"
+#include "lastrow_cluster.cuh"
 #include "rows.cuh"
 #include "tft_internal.h"
 
@@ -336,6 +337,10 @@ struct Launch {
     if ((e = set_smem<F>((const void*)k_row_inv<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_row_mul<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_lastrow_inv<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_lastrow_cluster<F, false>, mx)))
+      return e;
+    if ((e = set_smem<F>((const void*)k_lastrow_cluster<F, true>, mx)))
+      return e;
     TFT_PREP_LR(8);
     TFT_PREP_LR(9);
     TFT_PREP_LR(10);
@@ -515,6 +520,103 @@ struct Launch {
                                       col_smem_bytes<T>(P.c, cl), s>>>(
                      x, E, P.lr, (uint32_t)(P.a + 1), P.c, cl, 0, qe, 0,
                      omega_a_tw, in_scale_log, rt, ~0ull, nullptr));
+    }
+    return cudaGetLastError();
+  }
+
+  // ---- transforms without global scratch ---------------------------------
+  // Forward column pass over columns [q0, q1) with b_arg as the plan's b
+  // (b_arg = 0: columns of length a, no row a), no E.
+  static cudaError_t cols_fwd_range(T* x, uint64_t n, const Plan& P,
+                                    uint64_t b_arg, uint32_t q0, uint32_t q1,
+                                    const RT& rt, int nsm, cudaStream_t s,
+                                    const LaunchHook* H) {
+    const int cl = set_clog(P, q1 - q0, nsm);
+    const uint32_t C = 1u << cl;
+    const uint64_t units = (uint64_t)C << (P.c > 4 ? P.c - 4 : 0);
+    const int th = units >= 256 ? 256 : (units < 32 ? 32 : (int)units);
+    TFT_LAUNCH(K_COL_FWD,
+               k_col_fwd2<F, 256><<<(q1 - q0 + C - 1) / C, th,
+                                    col_smem_bytes<T>(P.c, cl), s>>>(
+                   x, n, x, nullptr, P.lr, P.a, b_arg, P.c, cl, q0, q1, rt));
+    return cudaGetLastError();
+  }
+  static cudaError_t lastrow_cluster(T* x, const Plan& P, T omega_a_tw,
+                                     bool inv, const RT& rt, cudaStream_t s,
+                                     const LaunchHook* H) {
+    const size_t sm = lastrow_cluster_smem<T>(P.lr, P.b);
+    if (inv)
+      TFT_LAUNCH(K_LASTROW_INV,
+                 (k_lastrow_cluster<F, true><<<kLastRowCluster, 512, sm, s>>>(
+                     x, P.lr, P.a, P.b, omega_a_tw, rt)));
+    else
+      TFT_LAUNCH(K_LASTROW_FWD,
+                 (k_lastrow_cluster<F, false><<<kLastRowCluster, 512, sm, s>>>(
+                     x, P.lr, P.a, P.b, omega_a_tw, rt)));
+    return cudaGetLastError();
+  }
+  // Forward TFT touching no memory but x: long columns (their row a in
+  // place), the last row from the raw short columns (lastrow_cluster.cuh),
+  // the short columns (length a), the full rows.
+  static cudaError_t forward_zs(T* x, uint64_t n, const Plan& P, T omega_a_tw,
+                                const RT& rt, int nsm, cudaStream_t s,
+                                const LaunchHook* H) {
+    if (P.small || P.b == 0)  // no ragged row: the plain forward uses no E
+      return forward(x, n, P, nullptr, rt, nsm, s, H, nullptr);
+    const uint32_t R = 1u << P.lr;
+    cudaError_t e = cols_fwd_range(x, n, P, P.b, 0, (uint32_t)P.b, rt, nsm,
+                                   s, H);
+    if (e == cudaSuccess) e = lastrow_cluster(x, P, omega_a_tw, false, rt, s, H);
+    if (e == cudaSuccess)
+      e = cols_fwd_range(x, n, P, 0, (uint32_t)P.b, R, rt, nsm, s, H);
+    if (e != cudaSuccess) return e;
+    if (use_v2(P)) return rows_fwd_v2(x, P, rt, nsm, s, H);
+    const uint32_t grid = (uint32_t)(P.a < (uint64_t)nsm * P.row_ctas_per_sm
+                                         ? P.a
+                                         : (uint64_t)nsm * P.row_ctas_per_sm);
+    TFT_LAUNCH(K_ROW_FWD, k_row_fwd<F><<<grid, 512, smem_row<F>(P.lr, 0), s>>>(
+                              x, nullptr, P.lr, P.a, 0, 0, rt));
+    return cudaGetLastError();
+  }
+  // Inverse TFT touching no memory but x: full rows, short columns, the
+  // last row with E_q from the recovered short columns, long columns.
+  static cudaError_t inverse_zs(T* x, uint64_t n, const Plan& P, T omega_a_tw,
+                                const RT& rt, int nsm, cudaStream_t s,
+                                const LaunchHook* H) {
+    if (P.small || P.b == 0)  // no ragged row: the plain inverse uses no E
+      return inverse(x, n, P, nullptr, omega_a_tw, rt, nsm, s, H);
+    const uint32_t R = 1u << P.lr;
+    if (use_v2(P)) {
+      cudaError_t e = rows_inv_v2(x, P, rt, nsm, s, H);
+      if (e != cudaSuccess) return e;
+    } else {
+      const uint32_t grid = (uint32_t)(P.a < (uint64_t)nsm * P.row_ctas_per_sm
+                                           ? P.a
+                                           : (uint64_t)nsm * P.row_ctas_per_sm);
+      TFT_LAUNCH(K_ROW_INV,
+                 k_row_inv<F><<<grid, 512, smem_row<F>(P.lr, 1), s>>>(
+                     x, P.lr, P.a, rt));
+    }
+    const uint32_t qb = (uint32_t)P.b;
+    {
+      const int cl = set_clog(P, R - qb, nsm);
+      const uint32_t C = 1u << cl;
+      TFT_LAUNCH(K_COL_INV,
+                 k_col_inv2<F, 256><<<(R - qb + C - 1) / C, 256,
+                                      col_smem_bytes<T>(P.c, cl), s>>>(
+                     x, nullptr, P.lr, (uint32_t)P.a, P.c, cl, qb, R, 0,
+                     omega_a_tw, 0, rt, ~0ull, nullptr));
+    }
+    cudaError_t e = lastrow_cluster(x, P, omega_a_tw, true, rt, s, H);
+    if (e != cudaSuccess) return e;
+    {
+      const int cl = set_clog(P, qb, nsm);
+      const uint32_t C = 1u << cl;
+      TFT_LAUNCH(K_COL_INV,
+                 k_col_inv2<F, 256><<<(qb + C - 1) / C, 256,
+                                      col_smem_bytes<T>(P.c, cl), s>>>(
+                     x, nullptr, P.lr, (uint32_t)(P.a + 1), P.c, cl, 0, qb, 0,
+                     omega_a_tw, 0, rt, ~0ull, nullptr));
     }
     return cudaGetLastError();
   }
@@ -811,7 +913,19 @@ static cudaError_t launch_tail(void* X, const void* S, uint64_t Q,
                               *(const RootTable<F::T>*)rt, nsm, s, hook,      \
                               aux);                                           \
   }                                                                           \
-  PlanSmem NAME##_plan_smem(const Plan& P) { return smem_of<F>(P); }
+  PlanSmem NAME##_plan_smem(const Plan& P) { return smem_of<F>(P); }        \
+  cudaError_t NAME##_forward_zs(void* x, uint64_t n, const Plan& P,           \
+                                uint64_t omega_a_tw, const void* rt, int nsm, \
+                                cudaStream_t s, const LaunchHook* hook) {     \
+    return Launch<F>::forward_zs((F::T*)x, n, P, (F::T)omega_a_tw,            \
+                                 *(const RootTable<F::T>*)rt, nsm, s, hook);  \
+  }                                                                           \
+  cudaError_t NAME##_inverse_zs(void* x, uint64_t n, const Plan& P,           \
+                                uint64_t omega_a_tw, const void* rt, int nsm, \
+                                cudaStream_t s, const LaunchHook* hook) {     \
+    return Launch<F>::inverse_zs((F::T*)x, n, P, (F::T)omega_a_tw,            \
+                                 *(const RootTable<F::T>*)rt, nsm, s, hook);  \
+  }
 
 #define TFT_DEFINE_FIELD_BATCH(F, NAME)                                       \
   cudaError_t NAME##_fold(void* d0, const void* s0, uint64_t n0, void* d1,    \

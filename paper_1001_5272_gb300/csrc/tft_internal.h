@@ -121,6 +121,14 @@ cudaError_t launch_forward(int prime, void* x, uint64_t n, const Plan& P,
 cudaError_t launch_inverse(int prime, void* x, uint64_t n, const Plan& P,
                            void* E, uint64_t omega_a_tw, const void* rt,
                            int nsm, cudaStream_t s, const LaunchHook* hook);
+// Forward / inverse TFT that read and write nothing but x (the ragged last
+// row from a thread-block cluster, lastrow_cluster.cuh).
+cudaError_t launch_forward_zs(int prime, void* x, uint64_t n, const Plan& P,
+                              uint64_t omega_a_tw, const void* rt, int nsm,
+                              cudaStream_t s, const LaunchHook* hook);
+cudaError_t launch_inverse_zs(int prime, void* x, uint64_t n, const Plan& P,
+                              uint64_t omega_a_tw, const void* rt, int nsm,
+                              cudaStream_t s, const LaunchHook* hook);
 cudaError_t launch_polymul(int prime, const void* a, uint64_t na,
                            const void* b, uint64_t nb, void* out,
                            const Plan& P, void* work, void* EA, void* EB,

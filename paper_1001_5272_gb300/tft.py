@@ -108,6 +108,8 @@ def load():
         "tft_kernel_name": (ctypes.c_char_p, [i32]),
         "tft_launch_count": (u64, [vp]),
         "tft_forward_noalloc": (i32, [i32, vp, u64, u32, vp]),
+        "tft_forward_noscratch": (i32, [i32, vp, u64, u32, vp]),
+        "tft_inverse_noscratch": (i32, [i32, vp, u64, u32, vp]),
         "tft_ctx_reserve_batch": (i32, [vp, u32, u64]),
         "tft_batch_work_words": (i32, [i32, ctypes.POINTER(PolymulDesc), u32,
                                        ctypes.POINTER(BatchParams),
@@ -417,6 +419,30 @@ def tft_forward_noalloc(prime, x, k=None, stream=None):
                                  n, k, _stream_handle(stream)),
            "tft_forward_noalloc")
     return x
+
+
+def _noscratch(name, prime, x, k, stream):
+    pid = prime_id(prime)
+    n = x.numel()
+    k = _default_k(n) if k is None else int(k)
+    L = load()
+    _check(getattr(L, name)(pid, _dev_ptr(x, int(L.tft_element_bytes(pid)),
+                                          "x"),
+                            n, k, _stream_handle(stream)), name)
+    return x
+
+
+def tft_forward_noscratch(prime, x, k=None, stream=None):
+    """In-place forward TFT (the result of tft_forward) that reads and
+    writes no device memory but x: no context, no scratch, no allocation;
+    the ragged last row comes from one 8-CTA cluster's shared memory."""
+    return _noscratch("tft_forward_noscratch", prime, x, k, stream)
+
+
+def tft_inverse_noscratch(prime, x, k=None, stream=None):
+    """In-place inverse TFT (the result of tft_inverse) that reads and
+    writes no device memory but x."""
+    return _noscratch("tft_inverse_noscratch", prime, x, k, stream)
 
 
 # ---------------------------------------------------------------------------
