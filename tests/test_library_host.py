@@ -88,6 +88,18 @@ def test_null_arguments_rejected_without_a_device():
     assert L.tft_element_bytes(9) == 0
 
 
+def test_noscratch_arguments_rejected_without_a_device():
+    # argument errors come back before any CUDA call
+    L = tft.load()
+    for fn in (L.tft_forward_noscratch, L.tft_inverse_noscratch):
+        assert fn(7, ctypes.c_void_p(16), 4, 2, None) == tft.TFT_EINVAL
+        assert fn(2, None, 4, 2, None) == tft.TFT_EINVAL
+        assert fn(2, ctypes.c_void_p(16), 0, 2, None) == tft.TFT_EINVAL
+        assert fn(2, ctypes.c_void_p(16), 5, 2, None) == tft.TFT_EINVAL  # n > 2^k
+        assert fn(2, ctypes.c_void_p(16), 4, 33, None) == tft.TFT_EINVAL  # k > K
+        assert fn(2, ctypes.c_void_p(24), 4, 2, None) == tft.TFT_EINVAL  # alignment
+
+
 def test_context_creation_without_gpu_fails_cleanly():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():
