@@ -39,7 +39,8 @@
  * context owns a fixed scratch of 2^18 + 2^14 words (rows of at most 2^14
  * words for transforms and products, one 2^18-point block for the
  * space-restricted product) plus, for products, one r-word work buffer, all
- * reserved when the context is created.  No call allocates device memory.
+ * reserved when the context is created.  No call allocates device memory;
+ * tft_forward_noscratch and tft_inverse_noscratch use none beyond x.
  *
  * Errors: argument errors are returned synchronously and nothing is
  * launched.  Launch failures return TFT_ECUDA.  Kernels run asynchronously
