@@ -2,8 +2,11 @@
 
 The generator is a workload convention, not part of the paper's method:
 what matters is that the oracle and the device produce the same operands
-(checked in the GPU tests) and that the stream behaves like Philox4x32-10's
-output should.  Pinned here, independently of the C code's own structure:
+(checked in the GPU tests) and that the stream is Philox4x32-10's.  Pinned
+here, independently of the C code's own structure:
+  * the round function against the generator's published known-answer
+    vectors (tests/golden/philox4x32_10_kat.txt), which fix it exactly: a
+    wrong constant, round count, key schedule or word order fails them;
   * the packing of the four words into v and the reduction mod p, against
     Python integers;
   * the counter layout (element index, operand, request split in two words)
@@ -14,11 +17,16 @@ output should.  Pinned here, independently of the C code's own structure:
     multiplication or XOR term breaks these).
 """
 
+import os
+
 import numpy as np
 import pytest
 
 from oracle import field as F
 from oracle import native as NV
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
 def words_to_int(x):
@@ -82,3 +90,13 @@ def test_philox_bit_balance_and_avalanche():
     # one input bit flips 64 of 128 output bits on average (binomial sd 5.7)
     assert abs(np.mean(flips) - 64) < 1.0
     assert min(flips) > 25
+
+
+def test_philox_known_answer_vectors():
+    rows = [l.split() for l in open(os.path.join(GOLDEN,
+                                                 "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for row in rows:
+        w = [int(v, 16) for v in row]
+        assert NV.philox4x32_10(w[0:4], w[4:6]) == tuple(w[6:10]), row

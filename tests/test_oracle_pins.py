@@ -341,6 +341,48 @@ def test_tft_polymul_equals_schoolbook_all_sizes_to_64(pr):
         T.tft_polymul(pr, a, b)
 
 
+def _exact_product(a, b, p):
+    # numpy's convolution over Python integers (object arrays): the exact
+    # integer product of the two polynomials, reduced mod p afterwards.
+    c = np.convolve(np.array([int(v) for v in a], dtype=object),
+                    np.array([int(v) for v in b], dtype=object))
+    return [int(v) % p for v in c]
+
+
+@pytest.mark.parametrize("pr", PRIMES, ids=lambda p: p.name)
+def test_conv_coeff_every_t_all_sizes_to_64(pr):
+    # orc_conv_coeff, the per-coefficient checker of the full-size GPU
+    # product tests: c_t = sum_i a_i b_{t-i} over the index pairs inside
+    # both operands (Section 5's product), for every t of every
+    # (na, nb) <= 64, against numpy's exact integer convolution; positions
+    # at and past r = na + nb - 1 are zero.  The first and last terms of the
+    # sum (lo and hi) are exercised by t = 0, t < min(na, nb), t in the
+    # middle band and t > max(na, nb).
+    rng = np.random.default_rng(53)
+    for na in range(1, 65):
+        for nb in range(1, 65):
+            a = rng.integers(0, pr.p, na, dtype=np.uint64)
+            b = rng.integers(0, pr.p, nb, dtype=np.uint64)
+            want = _exact_product(a, b, pr.p)
+            got = [NV.conv_coeff(pr, a, b, t) for t in range(na + nb + 1)]
+            assert got == want + [0, 0], (na, nb)
+
+
+@pytest.mark.parametrize("pr", PRIMES, ids=lambda p: p.name)
+def test_conv_coeff_random_t_large(pr):
+    rng = np.random.default_rng(59)
+    for na, nb in ((4096, 3), (1, 4096), (2500, 4096), (4096, 4096),
+                   (3001, 1777)):
+        a = rng.integers(0, pr.p, na, dtype=np.uint64)
+        b = rng.integers(0, pr.p, nb, dtype=np.uint64)
+        want = _exact_product(a, b, pr.p)
+        r = na + nb - 1
+        ts = {0, 1, na - 1, na, nb - 1, nb, r - 2, r - 1} | \
+            {int(t) for t in rng.integers(0, r, 40)}
+        for t in sorted(x for x in ts if 0 <= x < r):
+            assert NV.conv_coeff(pr, a, b, t) == want[t], (na, nb, t)
+
+
 @pytest.mark.parametrize("pr", PRIMES, ids=lambda p: p.name)
 def test_tft_polymul_random_sizes(pr):
     rng = np.random.default_rng(31)
