@@ -380,9 +380,11 @@ tft_status tft_forward_noalloc(tft_prime prime, void* x, uint64_t n,
  *   x, n, k, stream  as in tft_forward (x a 16-byte aligned device pointer
  *                    on the calling thread's current device).
  * Errors: as tft_forward, without the context's max_len (n up to 2^25 for
- * 2^64 - 2^32 + 1, min(2^K, 2^27) otherwise).  The first call on a device
- * configures the kernels for it (no allocation); make it before capturing
- * any stream on that device.  Calls may overlap freely (no shared state).
+ * 2^64 - 2^32 + 1, min(2^K, 2^27) otherwise).  The first call for a
+ * prime on a device reads the device's SM count and sets the kernels'
+ * shared-memory limits (host state behind a lock, no allocation); make it
+ * before capturing any stream on that device.  Calls may overlap freely on
+ * the GPU: they share no device memory.
  */
 tft_status tft_forward_noscratch(tft_prime prime, void* x, uint64_t n,
                                  uint32_t k, void* stream);

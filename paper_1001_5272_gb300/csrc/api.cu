@@ -246,49 +246,58 @@ static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoallocScratchWords
 
 namespace {
 
-struct NoallocDevice {
-  bool ready;
-  void* scratch;  // device address of g_noalloc_scratch on this device
-  int nsm;
-};
+// Once per (prime, device), with that device current: read the SM count
+// and set the kernels' shared-memory limits for `prime`.  Host state only;
+// no device memory is touched.
+std::mutex g_devinfo_mu;
+int g_devinfo_nsm[64];
 
-std::mutex g_noalloc_mu;
-NoallocDevice g_noalloc[64];
-
-// Once per device, with that device current: resolve the array's device
-// address (the host-side name is only a stand-in), read the SM count and set
-// the kernels' shared-memory limits for `prime`.
-tft_status noalloc_setup(int prime, int dev, NoallocDevice** out) {
+tft_status device_prepare(int prime, int dev, int* nsm_out) {
   if (dev < 0 || dev >= 64) return TFT_EINVAL;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  NoallocDevice& d = g_noalloc[dev];
-  if (!d.ready) {
-    void* p = nullptr;
-    if (note(cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess)
-      return TFT_ECUDA;
-    int nsm = 0;
-    if (note(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount,
-                                    dev)) != cudaSuccess)
-      return TFT_ECUDA;
-    d.scratch = p;
-    d.nsm = nsm;
-    d.ready = true;
-  }
   {
-    std::lock_guard<std::mutex> lk2(g_prep_mu);
-    if (!g_prepared[prime][dev]) {
-      int optin = 0;
-      if (note(cudaDeviceGetAttribute(&optin,
-                                      cudaDevAttrMaxSharedMemoryPerBlockOptin,
+    std::lock_guard<std::mutex> lk(g_devinfo_mu);
+    if (g_devinfo_nsm[dev] == 0) {
+      int nsm = 0;
+      if (note(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount,
                                       dev)) != cudaSuccess)
         return TFT_ECUDA;
-      if (note(prepare_kernels(prime, (size_t)optin)) != cudaSuccess)
-        return TFT_ECUDA;
-      g_prepared[prime][dev] = true;
+      g_devinfo_nsm[dev] = nsm;
     }
+    *nsm_out = g_devinfo_nsm[dev];
   }
-  *out = &d;
+  std::lock_guard<std::mutex> lk2(g_prep_mu);
+  if (!g_prepared[prime][dev]) {
+    int optin = 0;
+    if (note(cudaDeviceGetAttribute(&optin,
+                                    cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                    dev)) != cudaSuccess)
+      return TFT_ECUDA;
+    if (note(prepare_kernels(prime, (size_t)optin)) != cudaSuccess)
+      return TFT_ECUDA;
+    g_prepared[prime][dev] = true;
+  }
   return TFT_OK;
+}
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64];  // device address of g_noalloc_scratch per device
+
+// Once per device, with that device current: resolve the array's device
+// address (the host-side name is only a stand-in), then the device set-up
+// above.
+tft_status noalloc_setup(int prime, int dev, void** scratch, int* nsm) {
+  if (dev < 0 || dev >= 64) return TFT_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (note(cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess)
+        return TFT_ECUDA;
+      g_noalloc_addr[dev] = p;
+    }
+    *scratch = g_noalloc_addr[dev];
+  }
+  return device_prepare(prime, dev, nsm);
 }
 
 }  // namespace
@@ -307,17 +316,17 @@ tft_status tft_forward_noalloc(tft_prime prime, void* x, uint64_t n,
   if (need_words * pr.w > sizeof(g_noalloc_scratch)) return TFT_ERANGE;
   int dev = -1;
   if (note(cudaGetDevice(&dev)) != cudaSuccess) return TFT_ECUDA;
-  NoallocDevice* d = nullptr;
-  tft_status st = noalloc_setup((int)prime, dev, &d);
+  void* scratch = nullptr;
+  int nsm = 0;
+  tft_status st = noalloc_setup((int)prime, dev, &scratch, &nsm);
   if (st != TFT_OK) return st;
   // The root table is built on the stack; nothing is allocated.
   tft_ctx tmp;
   memset(&tmp, 0, sizeof(tmp));
   tmp.pr = pr;
   build_root_table(&tmp);
-  cudaError_t e = launch_forward((int)prime, x, n, P, d->scratch, tmp.rt,
-                                 d->nsm, (cudaStream_t)stream, nullptr,
-                                 nullptr);
+  cudaError_t e = launch_forward((int)prime, x, n, P, scratch, tmp.rt, nsm,
+                                 (cudaStream_t)stream, nullptr, nullptr);
   if (e != cudaSuccess) {
     note(e);
     return TFT_ECUDA;
@@ -335,8 +344,8 @@ static tft_status noscratch_transform(tft_prime prime, void* x, uint64_t n,
   if (!make_plan((int)prime, n, &P)) return TFT_ERANGE;
   int dev = -1;
   if (note(cudaGetDevice(&dev)) != cudaSuccess) return TFT_ECUDA;
-  NoallocDevice* d = nullptr;
-  tft_status st = noalloc_setup((int)prime, dev, &d);
+  int nsm = 0;
+  tft_status st = device_prepare((int)prime, dev, &nsm);
   if (st != TFT_OK) return st;
   // The root table is built on the stack; nothing is allocated and no
   // device memory but x is read or written.
@@ -346,9 +355,9 @@ static tft_status noscratch_transform(tft_prime prime, void* x, uint64_t n,
   build_root_table(&tmp);
   const uint64_t wa = P.small ? 0 : to_tw(pr, omega_s(pr, P.a));
   cudaError_t e =
-      inv ? launch_inverse_zs((int)prime, x, n, P, wa, tmp.rt, d->nsm,
+      inv ? launch_inverse_zs((int)prime, x, n, P, wa, tmp.rt, nsm,
                               (cudaStream_t)stream, nullptr)
-          : launch_forward_zs((int)prime, x, n, P, wa, tmp.rt, d->nsm,
+          : launch_forward_zs((int)prime, x, n, P, wa, tmp.rt, nsm,
                               (cudaStream_t)stream, nullptr);
   if (e != cudaSuccess) {
     note(e);

@@ -238,6 +238,44 @@ def test_batch_full_log_uniform_workload(ctxs):
             assert np.array_equal(c, NV.tft_polymul(pr, a, b)), i
 
 
+def _served_range_pairs():
+    # operand lengths of the served workload's range: log-uniform in
+    # [256, 2^20] (products up to r = 2^21 - 1), plus the extremes
+    rng = np.random.default_rng(61)
+    u = rng.random((2, 20))
+    L = np.clip(np.floor(256 * 4096.0 ** u), 256, 1 << 20).astype(np.int64)
+    pairs = [(int(x), int(y)) for x, y in zip(L[0], L[1])]
+    return pairs + [(1 << 20, 1 << 20), (1 << 20, 256), (256, 1 << 20),
+                    (256, 256), ((1 << 19) + 1, (1 << 19) + 3)]
+
+
+@pytest.mark.parametrize("params", [
+    None, {"small_log": 12, "lr": 11, "clog": 4}],
+    ids=["default", "sl12-lr11-c4"])
+def test_batch_goldilocks_served_length_range(ctxs, params):
+    # the served stream's products over 2^64 - 2^32 + 1 at full length
+    # range, under the default schedule and the one the serving benchmark
+    # runs: every product checked at a random point (Schwartz-Zippel), 24
+    # sampled coefficients of each by their defining sums, and the longest
+    # product (r = 2^21 - 1) plus three others element by element against
+    # the oracle's TFT product
+    pr = F.PGOLDILOCKS
+    pairs = _served_range_pairs()
+    A, B, C = run_batch(ctxs[pr.name], pr, pairs, params, seed=6)
+    rng = np.random.default_rng(67)
+    for i, (a, b, c) in enumerate(zip(A, B, C)):
+        r = c.size
+        z = int(rng.integers(2, pr.p - 1, dtype=np.uint64))
+        assert NV.eval_at(pr, c, z) == \
+            NV.eval_at(pr, a, z) * NV.eval_at(pr, b, z) % pr.p, pairs[i]
+        ts = {0, r - 1, a.size - 1, b.size - 1} | \
+            {int(t) for t in rng.integers(0, r, 20)}
+        for t in sorted(ts):
+            assert int(c[t]) == NV.conv_coeff(pr, a, b, t), (pairs[i], t)
+    for i in (len(pairs) - 5, len(pairs) - 4, len(pairs) - 1, 0):
+        assert np.array_equal(C[i], NV.tft_polymul(pr, A[i], B[i])), pairs[i]
+
+
 def test_batch_argument_errors(ctxs):
     tft = _lib()
     pr = F.PGOLDILOCKS

@@ -246,44 +246,61 @@ def _sample_indices(n, rng, extra=()):
 
 
 def test_config2_full_size(ctxs):
-    # n = 2^24 + 2^20 + 12345 over 2^64 - 2^32 + 1: forward on sampled
-    # outputs (the definition, one Horner evaluation each), inverse exactly
-    # (round trip), and the same launch configuration as the benchmark.
+    # n = 2^24 + 2^20 + 12345 over 2^64 - 2^32 + 1, in the launch
+    # configuration the benchmark times: every output element against the
+    # oracle's Algorithm 1 (run on a host thread while the GPU works),
+    # sampled outputs against the definition (one Horner evaluation each),
+    # and the inverse exactly (the round trip returns the input).
+    from concurrent.futures import ThreadPoolExecutor
     tft = _lib()
     pr = F.PGOLDILOCKS
     x = config2_input()
     n = x.size
-    plan = tft.tft_describe_plan(2, n)
-    R = 1 << plan["lr"]
-    t = to_dev(pr, x)
-    tft.tft_forward(ctxs[pr.name], t, 25)
-    torch.cuda.synchronize()
-    X = to_host(pr, t)
-    rng = np.random.default_rng(123)
-    # include the last row (s >= aR) and a row boundary
-    s = _sample_indices(n, rng, extra=(plan["a"] * R, plan["a"] * R - 1, R,
-                                       R - 1))
-    ref = NV.eval_tft_points(pr, x, s)
-    assert np.array_equal(X[s.astype(np.int64)], ref)
-    tft.tft_inverse(ctxs[pr.name], t, 25)
-    torch.cuda.synchronize()
-    assert np.array_equal(to_host(pr, t), x)
+    with ThreadPoolExecutor(1) as pool:
+        ref_fut = pool.submit(NV.alg1_tft, pr, x)
+        plan = tft.tft_describe_plan(2, n)
+        R = 1 << plan["lr"]
+        t = to_dev(pr, x)
+        tft.tft_forward(ctxs[pr.name], t, 25)
+        torch.cuda.synchronize()
+        X = to_host(pr, t)
+        rng = np.random.default_rng(123)
+        # include the last row (s >= aR) and a row boundary
+        s = _sample_indices(n, rng, extra=(plan["a"] * R, plan["a"] * R - 1,
+                                           R, R - 1))
+        ref = NV.eval_tft_points(pr, x, s)
+        assert np.array_equal(X[s.astype(np.int64)], ref)
+        tft.tft_inverse(ctxs[pr.name], t, 25)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_host(pr, t), x)
+        full = ref_fut.result()
+    bad = np.flatnonzero(X != full)
+    assert bad.size == 0, f"{bad.size} outputs differ, first at {bad[:8]}"
 
 
 def test_config3_full_size(ctxs):
-    # 3,000,000 x 5,000,001 over 2^64 - 2^32 + 1: C(z) = A(z) B(z) at random
-    # z (Schwartz-Zippel) and sampled coefficients by their defining sums.
+    # 3,000,000 x 5,000,001 over 2^64 - 2^32 + 1: every coefficient against
+    # the oracle's TFT product (Algorithm 1 on both zero-extended operands,
+    # pointwise product, Algorithm 2; run on a host thread while the GPU
+    # works), C(z) = A(z) B(z) at random z (Schwartz-Zippel) and sampled
+    # coefficients by their defining sums.
+    from concurrent.futures import ThreadPoolExecutor
     pr = F.PGOLDILOCKS
     a, b = config3_inputs()
-    c = gpu_polymul(ctxs, pr, a, b)
-    rng = np.random.default_rng(321)
-    for z in rng.integers(2, pr.p - 1, 2, dtype=np.uint64):
-        z = int(z)
-        assert NV.eval_at(pr, c, z) == \
-            NV.eval_at(pr, a, z) * NV.eval_at(pr, b, z) % pr.p
-    r = c.size
-    for t_ in [0, 1, 2, r - 1, r - 2, 2_999_999, 4_000_000]:
-        assert int(c[t_]) == NV.conv_coeff(pr, a, b, t_), t_
+    with ThreadPoolExecutor(1) as pool:
+        ref_fut = pool.submit(NV.tft_polymul, pr, a, b)
+        c = gpu_polymul(ctxs, pr, a, b)
+        rng = np.random.default_rng(321)
+        for z in rng.integers(2, pr.p - 1, 2, dtype=np.uint64):
+            z = int(z)
+            assert NV.eval_at(pr, c, z) == \
+                NV.eval_at(pr, a, z) * NV.eval_at(pr, b, z) % pr.p
+        r = c.size
+        for t_ in [0, 1, 2, r - 1, r - 2, 2_999_999, 4_000_000]:
+            assert int(c[t_]) == NV.conv_coeff(pr, a, b, t_), t_
+        full = ref_fut.result()
+    bad = np.flatnonzero(c != full)
+    assert bad.size == 0, f"{bad.size} coefficients differ, first at {bad[:8]}"
 
 
 @pytest.mark.parametrize("pid,na,nb", [

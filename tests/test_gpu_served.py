@@ -106,6 +106,54 @@ def test_served_mix_equals_alone_and_oracle(ctxs, pid):
             assert torch.equal(alone, keep[i]), i
 
 
+@pytest.mark.parametrize("params", [
+    None, {"small_log": 12, "lr": 11, "clog": 4}],
+    ids=["default", "sl12-lr11-c4"])
+def test_served_full_length_range(params):
+    # 64 requests of the served workload's shape over 2^64 - 2^32 + 1:
+    # 20,000 requests/s, operand lengths log-uniform in [256, 2^20], one
+    # request at the longest (r = 2^21 - 1), an 8 GB budget, under the
+    # default schedule and the one the serving benchmark runs.  Every
+    # product is checked at a random point (Schwartz-Zippel) and on sampled
+    # coefficients by their defining sums; the longest and every 16th
+    # element by element against the oracle and against the same request
+    # computed alone through the single-call product.
+    tft = _lib()
+    pid = 2
+    p = PRIMES[pid].p
+    t, na, nb = schedule(64, 20000.0, 256, 1 << 20, 71)
+    na[5] = nb[5] = 1 << 20
+    ids = np.arange(5000, 5064)
+    with tft.Context(pid, 0, max_len=1 << 21) as ctx:
+        keep = {i: torch.empty(int(na[i] + nb[i] - 1), dtype=torch.int64,
+                               device="cuda") for i in range(64)}
+        with tft.Server(ctx, 8 << 30, max_batch=4096, params=params) as srv:
+            done, st = srv.replay(ids, na, nb, t, seed=4, keep=keep)
+        torch.cuda.synchronize()
+        assert st["completed"] == 64
+        rng = np.random.default_rng(73)
+        for i in range(64):
+            a = NV.gen_operand(pid, 4, int(ids[i]), 0, int(na[i]))
+            b = NV.gen_operand(pid, 4, int(ids[i]), 1, int(nb[i]))
+            c = to_host(pid, keep[i])
+            r = c.size
+            z = int(rng.integers(2, p, dtype=np.uint64))
+            assert NV.eval_at(pid, c, z) == \
+                NV.eval_at(pid, a, z) * NV.eval_at(pid, b, z) % p, i
+            for t_ in {0, r - 1} | {int(v) for v in rng.integers(0, r, 6)}:
+                assert int(c[t_]) == NV.conv_coeff(pid, a, b, t_), (i, t_)
+            if i % 16 == 0 or i == 5:
+                assert np.array_equal(c, NV.tft_polymul(pid, a, b)), i
+                ta = torch.empty(int(na[i]), dtype=torch.int64, device="cuda")
+                tb = torch.empty(int(nb[i]), dtype=torch.int64, device="cuda")
+                tft.tft_generate(ctx, 4, int(ids[i]), 0, ta)
+                tft.tft_generate(ctx, 4, int(ids[i]), 1, tb)
+                alone = torch.empty_like(keep[i])
+                tft.tft_polymul(ctx, ta, tb, alone)
+                torch.cuda.synchronize()
+                assert torch.equal(alone, keep[i]), i
+
+
 def test_one_by_one_equals_batched_and_budget_holds(ctxs):
     # the comparison path gives the same products; a small budget forces
     # many batches and its peak stays within it

@@ -1,15 +1,21 @@
-"""The allocation-free forward TFT entry point, against the context one.
+"""The allocation-free forward TFT entry point, against the context one and
+against the oracle.
 
 Some callers cannot allocate device memory once they are running -- a
 serving loop whose device memory is reserved at start-up, or code inside an
 allocator callback -- so they cannot create a context.  tft_forward_noalloc
 serves them with a fixed device array as scratch.  These tests call it
-through the C ABI and require bit-for-bit the result of tft_forward (the
-tolerance of every parity test here is zero: the arithmetic is exact), on
-two calls in a row that reuse the shared array with different lengths.
-The file is named to be collected last, and each test also runs alone in a
-fresh process.
+through the C ABI and require bit-for-bit the result of tft_forward and of
+the oracle's Algorithm 1 (the tolerance of every parity test here is zero:
+the arithmetic is exact), on two calls in a row that reuse the shared array
+with different lengths.  The file is named to be collected last; the last
+test runs the others again in a fresh Python process, so that they also
+pass when the entry point's first call is the process's first.
 """
+
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -17,6 +23,8 @@ import pytest
 torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
+
+from oracle import native as NV  # noqa: E402
 
 P_GOLD = 2**64 - 2**32 + 1
 
@@ -51,12 +59,16 @@ def test_noalloc_matches_context_path_on_consecutive_calls(lib):
             lib.tft_forward_noalloc(2, got)
             torch.cuda.synchronize()
             assert torch.equal(got, want), f"call {i} (n={n}) differs"
+            ref = NV.alg1_tft(2, x)
+            assert np.array_equal(got.cpu().numpy().view(np.uint64), ref), \
+                f"call {i} (n={n}) differs from Algorithm 1"
 
 
 def test_noalloc_small_and_32bit_prime(lib):
-    # a single-CTA length and a 32-bit prime, also back to back
+    # a single-CTA length and a two-pass length of a 32-bit prime, back to
+    # back, against the context path and the oracle
+    p = 2013265921
     for pid, n, seed in ((1, 3001, 7), (1, 200003, 8)):
-        p = 2013265921
         x = np.random.default_rng(seed).integers(0, p, n, dtype=np.uint64)
         x32 = x.astype(np.uint32).view(np.int32)
         with lib.Context(pid, 0, max_len=n) as ctx:
@@ -66,6 +78,8 @@ def test_noalloc_small_and_32bit_prime(lib):
         lib.tft_forward_noalloc(pid, got)
         torch.cuda.synchronize()
         assert torch.equal(got, want), n
+        got64 = got.cpu().numpy().view(np.uint32).astype(np.uint64)
+        assert np.array_equal(got64, NV.alg1_tft(pid, x)), n
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit(lib):
@@ -80,3 +94,16 @@ def test_noalloc_rejects_sizes_beyond_its_limit(lib):
     with pytest.raises(lib.TFTError) as e:
         lib.tft_forward_noalloc(2, x[1:], k=10)       # misaligned
     assert e.value.status == lib.TFT_EINVAL
+
+
+@pytest.mark.skipif(os.environ.get("TFT_NOALLOC_CHILD") == "1",
+                    reason="already the fresh process")
+def test_noalloc_tests_pass_in_a_fresh_process(lib):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, TFT_NOALLOC_CHILD="1")
+    res = subprocess.run(
+        [sys.executable, "-m", "pytest", os.path.abspath(__file__), "-q",
+         "-m", "gpu", "-p", "no:cacheprovider"],
+        cwd=root, env=env, capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stdout[-3000:] + res.stderr[-2000:]
+    assert "3 passed" in res.stdout, res.stdout[-2000:]
