@@ -81,28 +81,71 @@ struct Goldilocks {
   }
   // x = lo + 2^64 (hl + 2^32 hh)  ==  lo - hh + (2^32 - 1) hl  (mod p), for
   // any 128-bit x; result in [0, 2^64).  t = lo - hh (a borrow costs EPS;
-  // t stays positive because lo - hh > -2^32), u = hl 2^32 - hl, then
-  // t + u with one carry worth EPS (t + u - 2^64 < 2^64 - 2^33, so adding
-  // EPS cannot carry).
+  // t stays positive because lo - hh > -2^32), then t + (2^32 - 1) hl on the
+  // multiply-add pipe (mad.lo.cc / madc.hi.cc, which keeps the ALU pipe,
+  // the busier one in the butterflies, free for the carry chains) with one
+  // carry worth EPS (t + (2^32 - 1) hl - 2^64 < 2^64 - 2^33, so adding EPS
+  // cannot carry).
   static __device__ __forceinline__ T reduce128(uint64_t lo, uint64_t hi) {
-    uint32_t t0, t1, m, u0, u1;
-    asm("sub.cc.u32 %0, %5, %8;\n\t"
-        "subc.cc.u32 %1, %6, 0;\n\t"
+    uint32_t t0, t1, m, c;
+    asm("sub.cc.u32 %0, %4, %7;\n\t"
+        "subc.cc.u32 %1, %5, 0;\n\t"
         "subc.u32 %2, 0, 0;\n\t"
         "sub.cc.u32 %0, %0, %2;\n\t"
         "subc.u32 %1, %1, 0;\n\t"
-        "sub.cc.u32 %3, 0, %7;\n\t"
-        "subc.u32 %4, %7, 0;\n\t"
+        "mad.lo.cc.u32 %0, %6, 0xffffffff, %0;\n\t"
+        "madc.hi.cc.u32 %1, %6, 0xffffffff, %1;\n\t"
+        "addc.u32 %3, 0, 0;\n\t"
+        "sub.u32 %3, 0, %3;\n\t"
         "add.cc.u32 %0, %0, %3;\n\t"
-        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %1, %1, 0;"
+        : "=&r"(t0), "=&r"(t1), "=&r"(m), "=&r"(c)
+        : "r"((uint32_t)lo), "r"((uint32_t)(lo >> 32)), "r"((uint32_t)hi),
+          "r"((uint32_t)(hi >> 32)));
+    return ((uint64_t)t1 << 32) | t0;
+  }
+  // [0, 2^64) -> [0, p): x >= p exactly when the high word is 2^32 - 1 and
+  // the low word is not 0, and then x - p has high word 0 and low word
+  // x0 - 1 (two predicated instructions instead of a 64-bit compare and
+  // subtract).
+  static __device__ __forceinline__ T canon_fast(T x) {
+    uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+    asm("{\n\t.reg .pred q;\n\t"
+        "setp.eq.u32 q, %1, 0xffffffff;\n\t"
+        "setp.ne.and.u32 q, %0, 0, q;\n\t"
+        "@q sub.u32 %0, %0, 1;\n\t"
+        "@q mov.u32 %1, 0;\n\t}"
+        : "+r"(x0), "+r"(x1));
+    return ((uint64_t)x1 << 32) | x0;
+  }
+  // a + b for a < 2^64 and b < p: a + b < 2^64 + p, so after a carry the
+  // wrapped sum is below p and adding EPS cannot carry again.
+  static __device__ __forceinline__ T add_c(T a, T b) {
+    uint32_t s0, s1, m;
+    asm("add.cc.u32 %0, %3, %5;\n\t"
+        "addc.cc.u32 %1, %4, %6;\n\t"
         "addc.u32 %2, 0, 0;\n\t"
         "sub.u32 %2, 0, %2;\n\t"
         "add.cc.u32 %0, %0, %2;\n\t"
         "addc.u32 %1, %1, 0;"
-        : "=&r"(t0), "=&r"(t1), "=&r"(m), "=&r"(u0), "=&r"(u1)
-        : "r"((uint32_t)lo), "r"((uint32_t)(lo >> 32)), "r"((uint32_t)hi),
-          "r"((uint32_t)(hi >> 32)));
-    return ((uint64_t)t1 << 32) | t0;
+        : "=&r"(s0), "=&r"(s1), "=&r"(m)
+        : "r"((uint32_t)a), "r"((uint32_t)(a >> 32)), "r"((uint32_t)b),
+          "r"((uint32_t)(b >> 32)));
+    return ((uint64_t)s1 << 32) | s0;
+  }
+  // a - b for a < 2^64 and b < p: after a borrow the wrapped difference is
+  // above 2^64 - p = EPS, so subtracting EPS cannot borrow again.
+  static __device__ __forceinline__ T sub_c(T a, T b) {
+    uint32_t d0, d1, m;
+    asm("sub.cc.u32 %0, %3, %5;\n\t"
+        "subc.cc.u32 %1, %4, %6;\n\t"
+        "subc.u32 %2, 0, 0;\n\t"
+        "sub.cc.u32 %0, %0, %2;\n\t"
+        "subc.u32 %1, %1, 0;"
+        : "=&r"(d0), "=&r"(d1), "=&r"(m)
+        : "r"((uint32_t)a), "r"((uint32_t)(a >> 32)), "r"((uint32_t)b),
+          "r"((uint32_t)(b >> 32)));
+    return ((uint64_t)d1 << 32) | d0;
   }
   static __device__ __forceinline__ T mul(T a, T b) {
     return reduce128(a * b, __umul64hi(a, b));
@@ -148,6 +191,11 @@ struct Mont32 {
   }
   static TFT_HD T half(T a) { return (a + ((a & 1) ? P : 0)) >> 1; }
   static TFT_HD T canon(T a) { return a; }  // always canonical
+  // the butterfly forms of Goldilocks (canonical second operand): values
+  // here are always canonical, so they are the plain operations
+  static TFT_HD T canon_fast(T a) { return a; }
+  static TFT_HD T add_c(T a, T b) { return add(a, b); }
+  static TFT_HD T sub_c(T a, T b) { return sub(a, b); }
   static TFT_HD T one_tw() { return ONE; }
 };
 

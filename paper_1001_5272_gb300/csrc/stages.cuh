@@ -170,7 +170,11 @@ __device__ __forceinline__ void powers(typename F::T (&pw)[1 << L],
 }
 
 // TOPCOPY: the upper half of the unit's inputs is known to be zero, so the
-// top level's butterflies (u, 0) -> (u, u) are copies.
+// top level's butterflies (u, 0) -> (u, u) are copies.  Each butterfly
+// brings its second term m (a product, or for k = 0 the entry itself) to
+// [0, p) first, so that the sum and the difference need a single carry
+// correction (F::add_c, F::sub_c); for the 32-bit fields these are the
+// plain operations.
 template <class F, int L, bool TOPCOPY = false>
 __device__ __forceinline__ void cnet_fwd(typename F::T (&x)[1 << L],
                                          const StageConsts<typename F::T>& K) {
@@ -186,10 +190,10 @@ __device__ __forceinline__ void cnet_fwd(typename F::T (&x)[1 << L],
       }
       const int k = i >> (d + 1);
       const T w = x[i + (1 << d)];
-      const T m = k == 0 ? w : F::mul_tw(w, K.c[k]);
+      const T m = F::canon_fast(k == 0 ? w : F::mul_tw(w, K.c[k]));
       const T u = x[i];
-      x[i] = F::add(u, m);
-      x[i + (1 << d)] = F::sub(u, m);
+      x[i] = F::add_c(u, m);
+      x[i + (1 << d)] = F::sub_c(u, m);
     }
   }
 }
@@ -206,9 +210,9 @@ __device__ __forceinline__ void cnet_inv2(typename F::T (&x)[1 << L],
     for (int i = 0; i < (1 << L); ++i) {
       if (i & (1 << d)) continue;
       const int k = i >> (d + 1);
-      const T X = x[i], Y = x[i + (1 << d)];
-      x[i] = F::add(X, Y);
-      const T df = F::sub(X, Y);
+      const T X = x[i], Y = F::canon_fast(x[i + (1 << d)]);
+      x[i] = F::add_c(X, Y);
+      const T df = F::sub_c(X, Y);
       x[i + (1 << d)] = k == 0 ? df : F::mul_tw(df, K.cu[k]);
     }
   }
