@@ -42,29 +42,116 @@ R_PROD = NA + NB - 1
 TFT_N = 2**24 + 2**20 + 12345
 P_GOLD = 2**64 - 2**32 + 1
 
-# Integer-multiply roofline (sm_103a unit counts and clock):
-# 152 SMs x 64 lanes of 32-bit IMAD per SM per clock x 2.07 GHz, and a
-# 64 x 64 -> 128-bit product needs 4 32 x 32 -> 64-bit partial products.
+# Multiply roofline.  A modular multiply of a field costs c_mul cycles of
+# the multiply (fmaheavy) pipe per warp-wide operation, measured with ncu
+# pipe counters on the calibration kernels (tft_calibrate, kind 0) and
+# recorded in profiles/calibration_pipes.md together with a hash of the
+# CUDA sources it was measured on.  Each SM sub-partition's multiply pipe
+# runs one cycle per clock, so the modmul bound of a field is
+# SMS * 4 * f_clk * 32 / c_mul per second.
 SMS = 152
-IMAD_LANES_PER_SM_CLK = 64
-SM_MAX_GHZ = 2.07
-MUL32_PER_MODMUL_GOLD = 4
+SMSP_PER_SM = 4
+SM_MAX_MHZ_FALLBACK = 2070.0
+PROFILES = os.path.join(ROOT, "profiles")
+CALIB_PROFILE = "calibration_pipes.md"
+TRAFFIC_PROFILE = "polymul_goldilocks_3000000x5000001_kernels.md"
+FIELD_NAMES = {0: "p998244353", 1: "p2013265921", 2: "goldilocks"}
+WORD_BYTES = {0: 4, 1: 4, 2: 8}
 
 
-# DRAM bytes (read + write) per launch of the product's kernels, from one ncu
-# capture of this workload's product (dram__bytes_read.sum +
-# dram__bytes_write.sum); to be re-taken whenever the kernel changes.
-NCU_TRAFFIC = {"k_row_mul": 128531712 + 50144512,
-               "k_col_fwd": (43047168 + 33781760 + 26969856 + 27250176) / 2,
-               "k_col_inv": 64190976 + 16820480}
-NCU_TRAFFIC_SOURCE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum "
-                      "on k_row_mul2 / k_col_fwd2 / k_col_inv2, this workload")
-# algorithmic bytes per launch: the row pass reads A' and B' and writes C'
-# (3 r words); a forward column pass reads its operand and writes r words
-# (mean of the two operands); the inverse column pass reads and writes r
-ALG_BYTES = {"k_row_mul": 3 * R_PROD * 8,
-             "k_col_fwd": ((NA + NB) // 2 + R_PROD) * 8,
-             "k_col_inv": 2 * R_PROD * 8}
+CALIB_SOURCES = ("calib.cu", "field.cuh", "stages.cuh")
+
+
+def sources_sha16(files=None):
+    """Hash of the library's CUDA/C++ sources (all of them, or the named
+    files of csrc/): a profile taken on other sources no longer describes
+    the kernels that run."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1001_5272_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")) and (files is None or
+                                                  f in files):
+            h.update(f.encode())
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_json(name):
+    """The first ```json block of profiles/<name>, or None."""
+    try:
+        text = open(os.path.join(PROFILES, name)).read()
+    except OSError:
+        return None
+    start = text.find("```json")
+    if start < 0:
+        return None
+    end = text.find("```", start + 7)
+    try:
+        return json.loads(text[start + 7:end])
+    except ValueError:
+        return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def modmul_peaks():
+    """Per field: the multiply-pipe bound in modmuls per second, from the
+    recorded c_mul and the SM clock, with where the numbers come from."""
+    prof = profile_json(CALIB_PROFILE) or {}
+    cmul = prof.get("c_mul_fmaheavy_cycles_per_warp_modmul") or {}
+    fresh = prof.get("sources_sha16") == sources_sha16(CALIB_SOURCES)
+    mhz = float(measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK)
+    out = {}
+    for pid, name in FIELD_NAMES.items():
+        c = cmul.get(name)
+        out[pid] = {
+            "c_mul": c,
+            "peak_modmul_per_s": (SMS * SMSP_PER_SM * mhz * 1e6 * 32 / c
+                                  if c else None),
+            "source": (f"profiles/{CALIB_PROFILE} (ncu pipe counters on "
+                       f"tft_calibrate kind 0, "
+                       f"{'current' if fresh else 'STALE'} sources); "
+                       f"{SMS} SMs x {SMSP_PER_SM} multiply pipes x "
+                       f"{mhz:.0f} MHz")
+            if c else "unavailable: no calibration profile",
+            "calibration_current": fresh}
+    return out
+
+
+def hbm_peak_gbs():
+    p = measured_peaks()
+    if p.get("hbm_gbs"):
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def leg_roofline(ms, modmuls, alg_bytes, pid):
+    """The roofline of one measured leg: the slower of its algorithmic
+    bytes at the HBM bandwidth and its algorithmic modmuls at the field's
+    multiply bound, against the measured time."""
+    bw, bw_src = hbm_peak_gbs()
+    pk = modmul_peaks()[pid]
+    t_hbm = alg_bytes / (bw * 1e9)
+    t_mul = modmuls / pk["peak_modmul_per_s"] if pk["peak_modmul_per_s"] \
+        else None
+    t = ms / 1e3
+    if t_mul is not None and t_mul >= t_hbm:
+        return {"bound": "alu", "achieved": modmuls / t / 1e9,
+                "peak": pk["peak_modmul_per_s"] / 1e9, "unit": "Gmodmul/s",
+                "frac": t_mul / t, "modmuls": modmuls,
+                "algorithmic_bytes": alg_bytes,
+                "hbm_frac": t_hbm / t}
+    return {"bound": "hbm", "achieved": alg_bytes / t / 1e9, "peak": bw,
+            "unit": "GB/s", "frac": t_hbm / t, "modmuls": modmuls,
+            "algorithmic_bytes": alg_bytes, "peak_source": bw_src,
+            "alu_frac": (t_mul / t) if t_mul else None}
 
 
 def env_int(name, default):
@@ -88,8 +175,15 @@ def parse_args():
     ap.add_argument("--served-params", default=None,
                     help="small_log,lr,clog for the served leg "
                          "(default: autotuned on a sample)")
-    ap.add_argument("--only", choices=("batched", "served", "restricted"),
+    ap.add_argument("--only", choices=("batched", "served", "restricted",
+                                       "calibrate"),
                     help="run one leg alone and print its JSON (profiling)")
+    ap.add_argument("--calib-iters", type=int, default=2000,
+                    help="loop count of the calibration kernels")
+    ap.add_argument("--ncu-summary", default=None, metavar="CSV",
+                    help="summarise an ncu --csv log (per kernel: launches, "
+                         "mean duration, share, per-launch metrics; per "
+                         "operation for the calibration kernels) and exit")
     ap.add_argument("--batch-count", type=int, default=None,
                     help="products in the batched leg (default 4096)")
     ap.add_argument("--batch-params", default=None,
@@ -363,34 +457,43 @@ def run_ours(args):
     # the dominant kernel is the longest launch: the two operands' column
     # passes run concurrently, so their summed live times overstate them
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_launch"])
-    t_launch = kernels[dom]["ms_per_launch"] / 1e3
     work = kernel_modmuls(plan, R_PROD)
-    mm = work.get(dom)
-    peak = SMS * IMAD_LANES_PER_SM_CLK * SM_MAX_GHZ * 1e9 / 1e12
-    achieved = (mm * MUL32_PER_MODMUL_GOLD / t_launch / 1e12
-                if mm else None)
-    roof = {"bound": "alu", "kernel": dom, "achieved": achieved,
-            "peak": peak, "unit": "Tmul32/s",
-            "frac": achieved / peak if achieved else None,
-            "traffic": NCU_TRAFFIC.get(dom),
-            "traffic_source": NCU_TRAFFIC_SOURCE if dom in NCU_TRAFFIC
-            else None,
-            "algorithmic_bytes_per_launch": ALG_BYTES.get(dom),
-            "work_per_launch": {"modmuls": mm,
-                                "mul32_per_modmul": MUL32_PER_MODMUL_GOLD},
-            "peak_source": "derived: 152 SMs x 64 IMAD lanes/clk x 2.07 GHz "
-                           "(unit counts and max clock)"}
+    # algorithmic bytes per launch: the row pass reads A' and B' and writes
+    # C' (3 r words); a forward column pass reads its operand and writes r
+    # words (mean of the two operands); the inverse column pass reads and
+    # writes r words
+    alg_launch = {"k_row_mul": 3 * R_PROD * 8,
+                  "k_col_fwd": ((NA + NB) // 2 + R_PROD) * 8,
+                  "k_col_inv": 2 * R_PROD * 8}
+    roof = leg_roofline(kernels[dom]["ms_per_launch"], work.get(dom, 0),
+                        alg_launch.get(dom, 0), 2)
+    roof["kernel"] = dom
+    roof["peak_source"] = modmul_peaks()[2]["source"] \
+        if roof["bound"] == "alu" else roof.get("peak_source")
+    roof["c_mul"] = modmul_peaks()[2]["c_mul"]
+    # DRAM traffic per launch from the committed ncu capture of this
+    # workload, if it was taken on the current sources
+    tprof = profile_json(TRAFFIC_PROFILE) or {}
+    ncu_name = {"k_row_mul": "k_row_mul2<goldilocks>",
+                "k_col_fwd": "k_col_fwd2<goldilocks>",
+                "k_col_inv": "k_col_inv2<goldilocks>"}.get(dom)
+    kk = (tprof.get("kernels") or {}).get(ncu_name) or {}
+    fresh = tprof.get("sources_sha16") == sources_sha16()
+    dram = kk.get("dram_bytes_per_launch")
+    roof["traffic"] = dram if (fresh and dram) else None
+    roof["traffic_source"] = (
+        f"profiles/{TRAFFIC_PROFILE}: dram__bytes_read.sum + "
+        f"dram__bytes_write.sum per launch of {ncu_name}" if dram and fresh
+        else ("stale: the capture predates the current sources" if dram
+              else "no capture"))
     # HBM view of the whole step for context
     alg_bytes = (NA + NB + R_PROD) * 8
-    hbm_frac = None
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        hbm_peak = float(peaks["hbm_gbs"])
-        hbm_src = "measured"
-    except Exception:
-        hbm_peak, hbm_src = 6800.0, "fallback"
+    hbm_peak, hbm_src = hbm_peak_gbs()
     step_s = statistics.mean(step_ms) / 1e3
     hbm_frac = alg_bytes / step_s / 1e9 / hbm_peak
+    bf_r = sum(tree_level_butterflies(R_PROD))
+    step_roof = leg_roofline(statistics.mean(step_ms), 3 * bf_r + R_PROD,
+                             alg_bytes, 2)
 
     # ---- single forward / inverse TFT (n = 2^24 + 2^20 + 12345) ----------
     extra = {}
@@ -425,6 +528,7 @@ def run_ours(args):
             kfi[name] = {k: v[0] for k, v in tft.tft_profile_read(ctx).items()}
             tft.tft_profile_enable(ctx, False)
         ok = bool(torch.equal(x.cpu(), torch.from_numpy(x_np.view(np.int64))))
+        bf_n = sum(tree_level_butterflies(TFT_N))
         inplace_b, padded_b = tft.tft_footprint(2, TFT_N, 25, 0)
         pin_b, ppad_b = tft.tft_footprint(2, R_PROD, 0, 1)
         extra = {
@@ -436,7 +540,11 @@ def run_ours(args):
                 "roundtrip_identity": ok,
                 "kernels_ms": kfi,
                 "device_bytes_inplace": inplace_b,
-                "device_bytes_padded_2^25": padded_b},
+                "device_bytes_padded_2^25": padded_b,
+                "roofline_forward": leg_roofline(
+                    statistics.median(fwd_ms), bf_n, 2 * TFT_N * 8, 2),
+                "roofline_inverse": leg_roofline(
+                    statistics.median(inv_ms), bf_n, 2 * TFT_N * 8, 2)},
             "polymul_footprint": {"device_bytes_inplace": pin_b,
                                   "device_bytes_padded": ppad_b},
         }
@@ -540,7 +648,10 @@ def run_ours(args):
                 "mcoeffs": R_PROD / statistics.median(t32) / 1e3,
                 "hbm_frac_of_algorithmic":
                     (NA + NB + R_PROD) * 4 / (statistics.median(t32) / 1e3)
-                    / 1e9 / hbm_peak}
+                    / 1e9 / hbm_peak,
+                "roofline": leg_roofline(statistics.median(t32),
+                                         3 * bf_r + R_PROD,
+                                         (NA + NB + R_PROD) * 4, 1)}
             del a32, b32, o32
         # ---- end to end through the host-buffer entry point --------------
         out_pin = torch.empty(R_PROD, dtype=torch.int64).pin_memory()
@@ -572,6 +683,7 @@ def run_ours(args):
 
         extra["batched_p2013265921_4096"] = batched_leg(args, tft, dev,
                                                         steps)
+        extra["calibration"] = calibration_leg(args, tft, dev)
         extra["served_goldilocks_20000rps"] = served_leg(args, tft, dev)
 
     cpu = None
@@ -598,6 +710,7 @@ def run_ours(args):
         "hbm_view": {"algorithmic_bytes_per_step": alg_bytes,
                      "frac_of_hbm": hbm_frac, "hbm_peak_gbs": hbm_peak,
                      "peak_source": hbm_src},
+        "step_roofline": step_roof,
         "kernels": kernels,
         "e2e": e2e,
         "cpu_baseline": cpu,
@@ -687,18 +800,50 @@ def batched_leg(args, tft, dev, steps):
         ev[2 * i + 1].record(cur)
     torch.cuda.synchronize()
     ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(steps)]
-    # spot check against the single-call path on a few products
-    ok = True
-    for i in (0, 1, len(A) // 2, len(A) - 1):
-        o = torch.empty(int(r[i]), dtype=torch.int32, device=dev)
-        tft.tft_polymul(ctx, prods[i][0], prods[i][1], o)
-        ok &= bool(torch.equal(o, prods[i][2]))
+    # the same products issued one call at a time through the single-call
+    # product on the same stream (what a caller without the batch API
+    # does), timed with CUDA events around all calls; every result must
+    # equal the batch's
+    tout1 = torch.empty_like(tout)
+    outs1 = [tout1[ooff[i]:ooff[i] + r[i]] for i in range(len(A))]
+    one_ms = []
+    for rep in range(1 + max(1, min(3, steps))):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        e0.record(cur)
+        for i in range(len(A)):
+            tft.tft_polymul(ctx, prods[i][0], prods[i][1], outs1[i], cur)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        if rep:
+            one_ms.append((e0.elapsed_time(e1),
+                           1e3 * (time.perf_counter() - w0)))
+    ok = all(bool(torch.equal(outs1[i], prods[i][2]))
+             for i in range(len(A)))
+    del tout1, outs1
     ctx.close()
     sum_r = int(r.sum())
     mean_ms = statistics.mean(ms)
+    one_dev = statistics.mean(v[0] for v in one_ms)
+    bf = {}
+    modmuls = 0
+    for x in r:
+        x = int(x)
+        if x not in bf:
+            bf[x] = sum(tree_level_butterflies(x))
+        modmuls += 3 * bf[x] + x
+    alg_bytes = int((na + nb + r).sum()) * 4
     return {"products": len(A), "sum_r": sum_r,
             "ms_per_batch": mean_ms, "ms_min": min(ms),
             "mcoeffs": sum_r / mean_ms / 1e3,
+            "roofline": leg_roofline(mean_ms, modmuls, alg_bytes, 1),
+            "one_call_at_a_time": {
+                "ms": one_dev, "mcoeffs": sum_r / one_dev / 1e3,
+                "host_wall_ms": statistics.mean(v[1] for v in one_ms),
+                "batched_over_one_by_one": one_dev / mean_ms,
+                "how": "tft_polymul per product on the same stream, CUDA "
+                       "events around all calls"},
             "params": params, "tuned_over": len(table),
             "launches_per_batch": launches_per_run,
             "graph": "all launches of one batch captured in one CUDA graph",
@@ -808,10 +953,132 @@ def served_leg(args, tft, dev):
     return out
 
 
+def calibration_leg(args, tft, dev):
+    """Rates of the calibration kernels (tft_calibrate), CUDA-event timed:
+    each field's modular multiply and the stage engine's 16-point unit, and
+    the 32-bit multiply-add and XOR lane rates, in registers on every SM
+    (8 CTAs of 256 threads per SM)."""
+    import torch
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(measured_peaks().get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK)
+    blocks = nsm * 8
+    buf = torch.empty(blocks * 256, dtype=torch.int64, device=dev)
+    cur = torch.cuda.current_stream()
+    names = {0: "modmul", 1: "mad32", 2: "xor32", 3: "unit16"}
+    out = {"blocks": blocks, "threads": 256, "sm_mhz_assumed": mhz}
+    for pid in (2, 1, 0):
+        with tft.Context(pid, dev, max_len=1 << 12) as c:
+            for kind in ((0, 3, 1, 2) if pid == 2 else (0, 3)):
+                it = args.calib_iters if kind != 3 else \
+                    max(1, args.calib_iters // 10)
+                for _ in range(2):
+                    tft.tft_calibrate(c, kind, it, blocks, buf, cur)
+                t = []
+                for _ in range(3):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(cur)
+                    ops = tft.tft_calibrate(c, kind, it, blocks, buf, cur)
+                    e1.record(cur)
+                    torch.cuda.synchronize()
+                    t.append(e0.elapsed_time(e1))
+                ms = statistics.median(t)
+                key = names[kind] + ("" if kind in (1, 2)
+                                     else "_" + FIELD_NAMES[pid])
+                out[key] = {"ops_per_launch": ops, "ms": ms,
+                            "g_ops_per_s": ops / ms / 1e6,
+                            "per_sm_per_clk": ops / (ms * 1e-3) / nsm /
+                            (mhz * 1e6)}
+    return out
+
+
+def kernel_key(full):
+    """Short key of a kernel name as ncu prints it: the function name, and
+    the field when it is a template argument ("k_row_mul2<goldilocks>")."""
+    t = full
+    for junk in ("void ", "<unnamed>::", "(anonymous namespace)::",
+                 "tftgb::"):
+        t = t.replace(junk, "")
+    t = t.strip()
+    cut = min([i for i in (t.find("<"), t.find("(")) if i >= 0] or [len(t)])
+    name = t[:cut].split("::")[-1]
+    targs = t[cut:t.find("(")] if t.find("(") > cut else ""
+    for tag, field in (("Goldilocks", "goldilocks"),
+                       ("2013265921", "p2013265921"),
+                       ("998244353", "p998244353")):
+        if tag in targs:
+            return f"{name}<{field}>"
+    return name
+
+
+def ncu_summary(path, calib_iters):
+    """Per kernel of an ncu --csv log: launches, mean duration, share of
+    the summed duration, and the mean of every other metric per launch;
+    DRAM bytes per launch when both DRAM counters were taken; for the
+    calibration kernels, counts per warp-wide operation (grid x 256 threads
+    x operations per thread / 32).  Printed with the hash of the current
+    sources."""
+    import csv
+    rows = list(csv.reader(open(path)))
+    hdr, per = None, {}
+    for row in rows:
+        if len(row) > 5 and row[0] == "ID":
+            hdr = row
+            continue
+        if not hdr or len(row) != len(hdr):
+            continue
+        d = dict(zip(hdr, row))
+        name = kernel_key(d["Kernel Name"])
+        lid = int(d["ID"])
+        try:
+            v = float(d["Metric Value"].replace(",", ""))
+        except ValueError:
+            continue
+        per.setdefault(name, {}).setdefault(lid, {})[d["Metric Name"]] = v
+    total = sum(sum(m.get("gpu__time_duration.sum", 0) for m in L.values())
+                for L in per.values()) or 1.0
+    calib = any(kernel_key(r[hdr.index("Kernel Name")]).startswith("k_calib")
+                for r in rows if hdr and len(r) == len(hdr))
+    out = {"sources_sha16": sources_sha16(CALIB_SOURCES if calib else None),
+           "kernels": {}}
+    for name, L in per.items():
+        mets = sorted({k for m in L.values() for k in m})
+        mean = {k: statistics.mean(m[k] for m in L.values() if k in m)
+                for k in mets}
+        e = {"launches": len(L),
+             "ms_mean": mean.get("gpu__time_duration.sum", 0) / 1e6,
+             "share": sum(m.get("gpu__time_duration.sum", 0)
+                          for m in L.values()) / total,
+             "per_launch": mean}
+        if "dram__bytes_read.sum" in mean and "dram__bytes_write.sum" in mean:
+            e["dram_bytes_per_launch"] = (mean["dram__bytes_read.sum"] +
+                                          mean["dram__bytes_write.sum"])
+        if name.startswith("k_calib") and "launch__grid_size" in mean:
+            unit = name.startswith("k_calib_unit")
+            it = max(1, calib_iters // 10) if unit else calib_iters
+            per_thread = it * (32 if unit else 8)
+            warp_ops = mean["launch__grid_size"] * 256 * per_thread / 32
+            e["per_warp_op"] = {k: mean[k] / warp_ops for k in mets
+                                if k.startswith("sm__")}
+        out["kernels"][name] = e
+    return out
+
+
 def main():
     args = parse_args()
+    if args.ncu_summary:
+        print(json.dumps(ncu_summary(args.ncu_summary, args.calib_iters),
+                         indent=1))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
+    if args.only == "calibrate":
+        import torch
+        from paper_1001_5272_gb300 import tft
+        torch.cuda.set_device(0)
+        out = calibration_leg(args, tft, 0)
+        print(json.dumps({"leg": "calibration", **out}), flush=True)
+        return 0
     if args.only == "batched":
         import torch
         from paper_1001_5272_gb300 import tft

@@ -463,6 +463,27 @@ tft_status tft_profile_read(tft_ctx* ctx, double* ms, uint64_t* launches);
 const char* tft_kernel_name(int kind);
 uint64_t tft_launch_count(tft_ctx* ctx);
 
+/*
+ * tft_calibrate: measurement aid for the roofline (the paper has no
+ * counterpart).  Launches one calibration kernel of `blocks` CTAs of 256
+ * threads on `stream`: kind 0 runs eight independent chains of the context
+ * field's modular multiply per thread (the multiply every butterfly uses),
+ * kind 1 chains of 32-bit multiply-adds, kind 2 chains of 32-bit XORs, kind 3
+ * the stage engine's 16-point unit (twist and constant network), each
+ * `iters` times in registers.  Pipe counters of a profiler divided by *ops
+ * give the cost of one operation in instructions and pipe cycles; the
+ * caller's CUDA-event time around the launch gives the rate.
+ *   out        device buffer of at least blocks * 256 * 8 bytes, 16-byte
+ *              aligned; receives one meaningless word per thread
+ *   ops        (may be NULL) operations per launch: modmuls, multiply-adds,
+ *              XORs, or butterflies (32 per unit)
+ * Errors: TFT_EINVAL for a null or small buffer, kind outside 0..3, zero
+ * blocks or iterations; TFT_ECUDA if the launch fails.
+ */
+tft_status tft_calibrate(tft_ctx* ctx, int kind, uint32_t iters,
+                         uint32_t blocks, void* out, uint64_t out_bytes,
+                         void* stream, uint64_t* ops);
+
 #ifdef __cplusplus
 }
 #endif

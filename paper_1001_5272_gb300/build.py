@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libtft_gb300.so")
 SOURCES = ["kernels_gold.cu", "kernels_p2013.cu", "kernels_p998.cu",
            "batch_gold.cu", "batch_p2013.cu", "batch_p998.cu",
            "dispatch.cu", "api.cu", "batch_api.cu", "gen.cu", "server.cu",
-           "restricted.cu"]
+           "restricted.cu", "calib.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -108,6 +108,8 @@ def load():
         "tft_kernel_name": (ctypes.c_char_p, [i32]),
         "tft_launch_count": (u64, [vp]),
         "tft_forward_noalloc": (i32, [i32, vp, u64, u32, vp]),
+        "tft_calibrate": (i32, [vp, i32, u32, u32, vp, u64, vp,
+                                ctypes.POINTER(u64)]),
         "tft_forward_noscratch": (i32, [i32, vp, u64, u32, vp]),
         "tft_inverse_noscratch": (i32, [i32, vp, u64, u32, vp]),
         "tft_ctx_reserve_batch": (i32, [vp, u32, u64]),
@@ -401,6 +403,19 @@ def tft_profile_read(ctx):
 
 def tft_launch_count(ctx):
     return int(load().tft_launch_count(ctx.handle))
+
+
+def tft_calibrate(ctx, kind, iters, blocks, out, stream=None):
+    """Launch one calibration kernel (include/tft.h); returns the number of
+    operations it performs.  `out` is a device tensor of at least
+    blocks * 256 * 8 bytes."""
+    ops = ctypes.c_uint64(0)
+    _check(load().tft_calibrate(ctx.handle, int(kind), int(iters),
+                                int(blocks), ctypes.c_void_p(out.data_ptr()),
+                                out.numel() * out.element_size(),
+                                _stream_handle(stream), ctypes.byref(ops)),
+           "tft_calibrate")
+    return int(ops.value)
 
 
 def tft_forward_noalloc(prime, x, k=None, stream=None):
