@@ -464,6 +464,21 @@ const char* tft_kernel_name(int kind);
 uint64_t tft_launch_count(tft_ctx* ctx);
 
 /*
+ * Allocation-failure injection (a testing aid; the paper has no
+ * counterpart).  Every device and pinned-host allocation the library makes
+ * (context creation, tft_ctx_reserve_batch, tft_server_create) goes through
+ * one host-side wrapper.  tft_debug_fail_allocation(n) makes the allocation
+ * after the next n successful ones fail once, as if the device were out of
+ * memory, without calling CUDA (n < 0 switches it off); the failing call
+ * returns TFT_ENOMEM after releasing what it had allocated.
+ * tft_debug_live_allocations returns how many of the library's allocations
+ * are currently held, so that a test can check that a failed call leaked
+ * nothing.  Neither touches the GPU.
+ */
+void tft_debug_fail_allocation(int64_t n);
+int64_t tft_debug_live_allocations(void);
+
+/*
  * tft_calibrate: measurement aid for the roofline (the paper has no
  * counterpart).  Launches one calibration kernel of `blocks` CTAs of 256
  * threads on `stream`: kind 0 runs eight independent chains of the context

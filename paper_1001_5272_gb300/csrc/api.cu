@@ -83,11 +83,11 @@ void ctx_release(tft_ctx* c) {
   if (c->aux.fork) cudaEventDestroy(c->aux.fork);
   if (c->aux.join) cudaEventDestroy(c->aux.join);
   if (c->aux.side) cudaStreamDestroy(c->aux.side);
-  if (c->stage) cudaFree(c->stage);
-  if (c->work) cudaFree(c->work);
-  if (c->scratch) cudaFree(c->scratch);
-  if (c->batch_tab) cudaFree(c->batch_tab);
-  if (c->batch_work) cudaFree(c->batch_work);
+  if (c->stage) dev_free(c->stage);
+  if (c->work) dev_free(c->work);
+  if (c->scratch) dev_free(c->scratch);
+  if (c->batch_tab) dev_free(c->batch_tab);
+  if (c->batch_work) dev_free(c->batch_work);
   free(c);
 }
 
@@ -168,6 +168,66 @@ namespace tftgb {
 cudaError_t note(cudaError_t e) {
   if (e != cudaSuccess) g_last_cuda_error = cudaGetErrorName(e);
   return e;
+}
+
+namespace {
+std::mutex g_alloc_mu;
+int64_t g_alloc_fail_after = -1;  // allocations to pass before one fails
+int64_t g_live_allocs = 0;
+
+// true: this allocation is to fail (the injected failure is used up)
+bool inject_failure() {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  if (g_alloc_fail_after < 0) return false;
+  if (g_alloc_fail_after == 0) {
+    g_alloc_fail_after = -1;
+    return true;
+  }
+  --g_alloc_fail_after;
+  return false;
+}
+void count_alloc(int64_t d) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_live_allocs += d;
+}
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (inject_failure()) return note(cudaErrorMemoryAllocation);
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return note(e);
+  }
+  count_alloc(1);
+  return e;
+}
+
+void dev_free(void* p) {
+  if (!p) return;
+  cudaFree(p);
+  count_alloc(-1);
+}
+
+cudaError_t host_malloc_pinned(void** p, size_t bytes) {
+  *p = nullptr;
+  if (inject_failure()) return note(cudaErrorMemoryAllocation);
+  const cudaError_t e = cudaMallocHost(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return note(e);
+  }
+  count_alloc(1);
+  return e;
+}
+
+void host_free_pinned(void* p) {
+  if (!p) return;
+  cudaFreeHost(p);
+  count_alloc(-1);
 }
 
 tft_status from_cuda(tft_ctx* ctx, cudaError_t e) {
@@ -304,6 +364,16 @@ tft_status noalloc_setup(int prime, int dev, void** scratch, int* nsm) {
 
 extern "C" {
 
+void tft_debug_fail_allocation(int64_t n) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc_fail_after = n < 0 ? -1 : n;
+}
+
+int64_t tft_debug_live_allocations(void) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return g_live_allocs;
+}
+
 tft_status tft_forward_noalloc(tft_prime prime, void* x, uint64_t n,
                                uint32_t k, void* stream) {
   if (!valid_prime((int)prime) || !x || n == 0) return TFT_EINVAL;
@@ -437,13 +507,13 @@ tft_status tft_ctx_create(tft_prime prime, int device, uint64_t max_len,
     return TFT_ECUDA;
   }
   const size_t w = pr.w;
-  if (cudaMalloc(&c->scratch, kCtxScratchWords * w) != cudaSuccess ||
-      cudaMalloc(&c->work, max_len * w) != cudaSuccess) {
+  if (dev_malloc((void**)&c->scratch, kCtxScratchWords * w) != cudaSuccess ||
+      dev_malloc((void**)&c->work, max_len * w) != cudaSuccess) {
     ctx_release(c);
     return TFT_ENOMEM;
   }
   if (flags & TFT_CTX_HOST_STAGING) {
-    if (cudaMalloc(&c->stage, 3 * stage_slot_bytes(c)) != cudaSuccess) {
+    if (dev_malloc((void**)&c->stage, 3 * stage_slot_bytes(c)) != cudaSuccess) {
       ctx_release(c);
       return TFT_ENOMEM;
     }

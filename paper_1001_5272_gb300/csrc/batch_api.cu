@@ -181,21 +181,21 @@ tft_status tft_ctx_reserve_batch(tft_ctx* ctx, uint32_t max_products,
   if (!ctx || max_products == 0) return TFT_EINVAL;
   DeviceGuard g(ctx->device);
   if (!g.ok) return TFT_ECUDA;
-  if (ctx->batch_tab) cudaFree(ctx->batch_tab);
-  if (ctx->batch_work) cudaFree(ctx->batch_work);
+  if (ctx->batch_tab) dev_free(ctx->batch_tab);
+  if (ctx->batch_work) dev_free(ctx->batch_work);
   ctx->batch_tab = ctx->batch_work = nullptr;
   ctx->batch_ready = 0;
   ctx->batch_tab_bytes =
       (uint64_t)max_products * (sizeof(BatchLarge) + sizeof(BatchSmall)) +
       256;
-  if (cudaMalloc(&ctx->batch_tab, ctx->batch_tab_bytes) != cudaSuccess) {
+  if (dev_malloc((void**)&ctx->batch_tab, ctx->batch_tab_bytes) != cudaSuccess) {
     ctx->batch_tab = nullptr;
     return TFT_ENOMEM;
   }
   ctx->batch_work_words = work_words;
   if (work_words &&
-      cudaMalloc(&ctx->batch_work, work_words * ctx->pr.w) != cudaSuccess) {
-    cudaFree(ctx->batch_tab);
+      dev_malloc((void**)&ctx->batch_work, work_words * ctx->pr.w) != cudaSuccess) {
+    dev_free(ctx->batch_tab);
     ctx->batch_tab = ctx->batch_work = nullptr;
     return TFT_ENOMEM;
   }

@@ -68,6 +68,14 @@ namespace tftgb {
 
 // Record a CUDA error for tft_last_cuda_error; returns e.
 cudaError_t note(cudaError_t e);
+// Every device and pinned-host allocation of the library goes through these
+// (tft_debug_fail_allocation injects a failure here; the live count shows
+// leaks).  A failed allocation leaves *p null and clears the runtime's
+// last-error state, so a later launch check does not report it again.
+cudaError_t dev_malloc(void** p, size_t bytes);
+void dev_free(void* p);
+cudaError_t host_malloc_pinned(void** p, size_t bytes);
+void host_free_pinned(void* p);
 // TFT_OK on success; otherwise records e, marks the context and returns
 // TFT_ECUDA.
 tft_status from_cuda(tft_ctx* ctx, cudaError_t e);

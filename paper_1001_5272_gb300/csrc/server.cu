@@ -214,15 +214,15 @@ namespace {
 void server_release(tft_server* s) {
   for (Slot& sl : s->slot) {
     if (sl.done) cudaEventDestroy(sl.done);
-    if (sl.htab) cudaFreeHost(sl.htab);
-    if (sl.dtab) cudaFree(sl.dtab);
+    if (sl.htab) host_free_pinned(sl.htab);
+    if (sl.dtab) dev_free(sl.dtab);
   }
   if (s->t0) cudaEventDestroy(s->t0);
   if (s->aux.fork) cudaEventDestroy(s->aux.fork);
   if (s->aux.join) cudaEventDestroy(s->aux.join);
   if (s->aux.side) cudaStreamDestroy(s->aux.side);
   if (s->stream) cudaStreamDestroy(s->stream);
-  if (s->base) cudaFree(s->base);
+  if (s->base) dev_free(s->base);
   delete s;
 }
 
@@ -263,7 +263,7 @@ tft_status tft_server_create(tft_ctx* ctx, uint64_t budget_bytes,
   }
   s->optin = (size_t)optin;
   s->arena.init(budget_bytes, kBlockAlign);
-  if (cudaMalloc(&s->base, s->arena.size) != cudaSuccess) {
+  if (dev_malloc((void**)&s->base, s->arena.size) != cudaSuccess) {
     s->base = nullptr;
     server_release(s);
     return TFT_ENOMEM;
@@ -285,8 +285,8 @@ tft_status tft_server_create(tft_ctx* ctx, uint64_t budget_bytes,
   for (Slot& sl : s->slot) {
     if (!ok) break;
     sl.tab_bytes = tb;
-    ok = cudaMalloc(&sl.dtab, tb) == cudaSuccess &&
-         cudaMallocHost(&sl.htab, tb) == cudaSuccess &&
+    ok = dev_malloc((void**)&sl.dtab, tb) == cudaSuccess &&
+         host_malloc_pinned((void**)&sl.htab, tb) == cudaSuccess &&
          note(cudaEventCreate(&sl.done)) == cudaSuccess;
   }
   if (!ok) {

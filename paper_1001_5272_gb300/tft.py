@@ -110,6 +110,8 @@ def load():
         "tft_forward_noalloc": (i32, [i32, vp, u64, u32, vp]),
         "tft_calibrate": (i32, [vp, i32, u32, u32, vp, u64, vp,
                                 ctypes.POINTER(u64)]),
+        "tft_debug_fail_allocation": (None, [ctypes.c_int64]),
+        "tft_debug_live_allocations": (ctypes.c_int64, []),
         "tft_forward_noscratch": (i32, [i32, vp, u64, u32, vp]),
         "tft_inverse_noscratch": (i32, [i32, vp, u64, u32, vp]),
         "tft_ctx_reserve_batch": (i32, [vp, u32, u64]),
@@ -157,7 +159,8 @@ def _header_functions():
     hdr = os.path.join(os.path.dirname(_HERE), "include", "tft.h")
     text = open(hdr).read()
     return re.findall(
-        r"^\s*(?:tft_status|uint32_t|uint64_t|const char\*)\s+(tft_\w+)\(",
+        r"^\s*(?:tft_status|uint32_t|uint64_t|int64_t|void|const char\*)"
+        r"\s+(tft_\w+)\(",
         text, flags=re.M)
 
 
@@ -403,6 +406,16 @@ def tft_profile_read(ctx):
 
 def tft_launch_count(ctx):
     return int(load().tft_launch_count(ctx.handle))
+
+
+def tft_debug_fail_allocation(n):
+    """Make the library's allocation after the next n successful ones fail
+    once (n < 0: off); see include/tft.h."""
+    load().tft_debug_fail_allocation(int(n))
+
+
+def tft_debug_live_allocations():
+    return int(load().tft_debug_live_allocations())
 
 
 def tft_calibrate(ctx, kind, iters, blocks, out, stream=None):

@@ -199,3 +199,12 @@ def test_restricted_schedule_follows_algorithm_3():
         assert tail == q and r - tail < 2 ** 18, (r, tail)
     with pytest.raises(tft.TFTError):
         tft.tft_restricted_schedule(0)
+
+
+def test_allocation_injection_hooks_without_a_device():
+    # the hooks are host state only: nothing is allocated here, and arming
+    # and disarming an injected failure touches no device
+    assert tft.tft_debug_live_allocations() == 0
+    tft.tft_debug_fail_allocation(2)
+    tft.tft_debug_fail_allocation(-1)
+    assert tft.tft_debug_live_allocations() == 0
