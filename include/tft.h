@@ -464,6 +464,52 @@ const char* tft_kernel_name(int kind);
 uint64_t tft_launch_count(tft_ctx* ctx);
 
 /*
+ * Pieces of a transform held in parts -- the data plane of a transform
+ * sharded over several GPUs (one part per rank).  The library's transforms
+ * of length n = a R + b (R = 2^lr, the split tft_describe_plan reports;
+ * requires a plan that is not single-CTA, with lr >= 8) are the row/column
+ * form of Algorithms 1 and 2, the split that Section 1.3 credits to the
+ * cache-friendly TFT: column q holds x_{q + tR}, t <= a (long, q < b) or
+ * t < a (short); every column is its own TFT, full row rho < a is block rho
+ * of the length-2^k network, and the ragged last row (row a, b outputs)
+ * needs E_q = C_q(omega_a) of the short columns.  With P = parts (a power
+ * of two, P <= R) and W = R / P, part p holds
+ *   - column block p: columns [p W, (p + 1) W) as an (a + 1) x W array at
+ *     row stride W, element (t, j) = x_{pW + j + tR}; its long columns are
+ *     j < b_p = min(max(b - p W, 0), W), and row a is used only for them;
+ *   - E_p: W words, the block's share of E (entries j >= b_p);
+ *   - full rows [rho_p, rho_{p+1}), rho_p = p a / P (integer division):
+ *     positions rho R .. rho R + R - 1 of the transform, R words each;
+ *   - for the last part, the ragged row: an R-word row buffer (first b
+ *     words) with the R-word E gathered from all parts.
+ * Forward TFT: tft_shard_columns(inverse 0) on every block; the caller
+ * moves block rows to the parts owning them (an all-to-all) and gathers
+ * the long columns' row a and every E_p into the last part's row and E;
+ * tft_shard_rows(0) on every part's rows; tft_shard_last_row(0) on the last
+ * part.  Inverse: tft_shard_rows(1); move rows back into column blocks;
+ * tft_shard_columns(1, which 0) (short columns, writes E_p); gather E and
+ * tft_shard_last_row(1) on the last part, whose row then holds the long
+ * columns' entries of row a; scatter them into the blocks;
+ * tft_shard_columns(1, which 1) (long columns).  Results are bit for bit
+ * those of tft_forward / tft_inverse.
+ *   inverse   0 forward, 1 inverse; which (inverse columns only): 0 the
+ *             block's short columns, 1 its long ones
+ *   block, rows, row, E   16-byte aligned device pointers as above (E may
+ *             be NULL where the block has no short columns or b = 0)
+ *   rho_begin, count      the part's rows rho_begin .. + count - 1 (< a)
+ * Errors: TFT_EINVAL for a bad argument (parts not a power of two, part >=
+ * parts, a single-CTA plan, rows beyond a); TFT_ERANGE for n beyond the
+ * supported maximum.  No call allocates; the context's scratch is unused.
+ */
+tft_status tft_shard_columns(tft_ctx* ctx, int inverse, int which,
+                             void* block, uint64_t n, uint32_t parts,
+                             uint32_t part, void* E, void* stream);
+tft_status tft_shard_rows(tft_ctx* ctx, int inverse, void* rows, uint64_t n,
+                          uint64_t rho_begin, uint64_t count, void* stream);
+tft_status tft_shard_last_row(tft_ctx* ctx, int inverse, void* row,
+                              const void* E, uint64_t n, void* stream);
+
+/*
  * Allocation-failure injection (a testing aid; the paper has no
  * counterpart).  Every device and pinned-host allocation the library makes
  * (context creation, tft_ctx_reserve_batch, tft_server_create) goes through

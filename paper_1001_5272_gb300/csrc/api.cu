@@ -557,6 +557,78 @@ tft_status tft_inverse(tft_ctx* ctx, void* X, uint64_t n, uint32_t k,
                                        (cudaStream_t)stream, &ctx->hook));
 }
 
+// The plan of a transform of length n held in `parts` parts, and the
+// column block plan of part `part` (row stride W = R / parts, b = the
+// block's long columns).
+static tft_status shard_plans(tft_ctx* ctx, uint64_t n, uint32_t parts,
+                              uint32_t part, Plan* P, Plan* Pc) {
+  if (!ctx || n == 0 || parts == 0 || (parts & (parts - 1)) ||
+      part >= parts)
+    return TFT_EINVAL;
+  if (!make_plan(ctx->prime, n, P)) return TFT_ERANGE;
+  if (P->small || P->lr < 8) return TFT_EINVAL;
+  int lp = 0;
+  while ((1u << lp) < parts) ++lp;
+  if (lp > P->lr) return TFT_EINVAL;
+  *Pc = *P;
+  Pc->lr = P->lr - lp;
+  const uint64_t W = 1ull << Pc->lr;
+  const uint64_t q0 = (uint64_t)part * W;
+  Pc->b = P->b > q0 ? (P->b - q0 < W ? P->b - q0 : W) : 0;
+  return TFT_OK;
+}
+
+tft_status tft_shard_columns(tft_ctx* ctx, int inverse, int which,
+                             void* block, uint64_t n, uint32_t parts,
+                             uint32_t part, void* E, void* stream) {
+  Plan P, Pc;
+  tft_status st = shard_plans(ctx, n, parts, part, &P, &Pc);
+  if (st != TFT_OK) return st;
+  if (!block || !aligned16(block) || (E && !aligned16(E))) return TFT_EINVAL;
+  if (inverse && which != 0 && which != 1) return TFT_EINVAL;
+  const uint64_t W = 1ull << Pc.lr;
+  // E is read or written for the block's short columns when the transform
+  // has a ragged last row
+  const int want_E = P.b > 0 && Pc.b < W && (!inverse || which == 0);
+  if (want_E && !E) return TFT_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  return from_cuda(ctx, launch_shard_cols(ctx->prime, inverse ? 1 : 0, which,
+                                          block, Pc, E, want_E,
+                                          omega_a_tw(ctx, P), ctx->rt,
+                                          ctx->nsm, (cudaStream_t)stream,
+                                          &ctx->hook));
+}
+
+tft_status tft_shard_rows(tft_ctx* ctx, int inverse, void* rows, uint64_t n,
+                          uint64_t rho_begin, uint64_t count, void* stream) {
+  Plan P, Pc;
+  tft_status st = shard_plans(ctx, n, 1, 0, &P, &Pc);
+  if (st != TFT_OK) return st;
+  if ((count && (!rows || !aligned16(rows))) || rho_begin + count > P.a)
+    return TFT_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  return from_cuda(ctx, launch_shard_rows(ctx->prime, inverse ? 1 : 0, rows,
+                                          count, rho_begin, P.lr, ctx->rt,
+                                          ctx->nsm, (cudaStream_t)stream,
+                                          &ctx->hook));
+}
+
+tft_status tft_shard_last_row(tft_ctx* ctx, int inverse, void* row,
+                              const void* E, uint64_t n, void* stream) {
+  Plan P, Pc;
+  tft_status st = shard_plans(ctx, n, 1, 0, &P, &Pc);
+  if (st != TFT_OK) return st;
+  if (P.b == 0) return TFT_OK;  // no ragged row
+  if (!row || !E || !aligned16(row) || !aligned16(E)) return TFT_EINVAL;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  return from_cuda(ctx, launch_shard_last(ctx->prime, inverse ? 1 : 0, row, E,
+                                          P.a, P.b, P.lr, ctx->rt,
+                                          (cudaStream_t)stream, &ctx->hook));
+}
+
 tft_status tft_polymul(tft_ctx* ctx, const void* a, uint64_t na,
                        const void* b, uint64_t nb, void* out, void* stream) {
   if (!ctx || !a || !b || !out || na == 0 || nb == 0) return TFT_EINVAL;

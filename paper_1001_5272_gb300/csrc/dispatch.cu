@@ -24,6 +24,17 @@ namespace tftgb {
   cudaError_t NAME##_inverse_zs(void* x, uint64_t n, const Plan& P,           \
                                 uint64_t omega_a_tw, const void* rt, int nsm, \
                                 cudaStream_t s, const LaunchHook* hook);      \
+  cudaError_t NAME##_shard_cols(int dir, int which, void* blk, const Plan& Pc, \
+                                void* E, int want_E, uint64_t omega_a_tw,     \
+                                const void* rt, int nsm, cudaStream_t s,      \
+                                const LaunchHook* hook);                      \
+  cudaError_t NAME##_shard_rows(int dir, void* rows, uint64_t count,          \
+                                uint64_t rho_off, int lr, const void* rt,     \
+                                int nsm, cudaStream_t s,                      \
+                                const LaunchHook* hook);                      \
+  cudaError_t NAME##_shard_last(int dir, void* row, const void* E, uint64_t a, \
+                                uint64_t b, int lr, const void* rt,           \
+                                cudaStream_t s, const LaunchHook* hook);      \
   cudaError_t NAME##_batch(const BatchLaunch& B, const void* rt, int nsm,   \
                            cudaStream_t s, const LaunchHook* hook,          \
                            const AuxStreams* aux);                          \
@@ -147,6 +158,40 @@ cudaError_t launch_tail(int prime, void* X, const void* S, uint64_t Q,
   TFT_BY_PRIME(prime, p998_tail(X, S, Q, lo, hi, mul, nsm, s),
                p2013_tail(X, S, Q, lo, hi, mul, nsm, s),
                gold_tail(X, S, Q, lo, hi, mul, nsm, s));
+}
+
+cudaError_t launch_shard_cols(int prime, int dir, int which, void* blk,
+                              const Plan& Pc, void* E, int want_E,
+                              uint64_t omega_a_tw, const void* rt, int nsm,
+                              cudaStream_t s, const LaunchHook* hook) {
+  TFT_BY_PRIME(prime,
+               p998_shard_cols(dir, which, blk, Pc, E, want_E, omega_a_tw, rt,
+                               nsm, s, hook),
+               p2013_shard_cols(dir, which, blk, Pc, E, want_E, omega_a_tw,
+                                rt, nsm, s, hook),
+               gold_shard_cols(dir, which, blk, Pc, E, want_E, omega_a_tw, rt,
+                               nsm, s, hook));
+}
+
+cudaError_t launch_shard_rows(int prime, int dir, void* rows, uint64_t count,
+                              uint64_t rho_off, int lr, const void* rt,
+                              int nsm, cudaStream_t s,
+                              const LaunchHook* hook) {
+  TFT_BY_PRIME(prime,
+               p998_shard_rows(dir, rows, count, rho_off, lr, rt, nsm, s,
+                               hook),
+               p2013_shard_rows(dir, rows, count, rho_off, lr, rt, nsm, s,
+                                hook),
+               gold_shard_rows(dir, rows, count, rho_off, lr, rt, nsm, s,
+                               hook));
+}
+
+cudaError_t launch_shard_last(int prime, int dir, void* row, const void* E,
+                              uint64_t a, uint64_t b, int lr, const void* rt,
+                              cudaStream_t s, const LaunchHook* hook) {
+  TFT_BY_PRIME(prime, p998_shard_last(dir, row, E, a, b, lr, rt, s, hook),
+               p2013_shard_last(dir, row, E, a, b, lr, rt, s, hook),
+               gold_shard_last(dir, row, E, a, b, lr, rt, s, hook));
 }
 
 }  // namespace tftgb

@@ -178,7 +178,7 @@ k_row_inv(typename F::T* X, int lr, uint64_t a, RootTable<typename F::T> rt) {
 // recovered inputs (the long columns' last transform values).
 template <class F>
 __global__ void __launch_bounds__(512)
-k_lastrow_inv(typename F::T* X, const typename F::T* __restrict__ E, int lr,
+k_lastrow_inv(typename F::T* row, const typename F::T* __restrict__ E, int lr,
               uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
   using T = typename F::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -190,7 +190,6 @@ k_lastrow_inv(typename F::T* X, const typename F::T* __restrict__ E, int lr,
   T* Wih = W + R / 2;
   T* L = Wih + R / 2;
   build_base_tables<F>(W, Wih, lr, s_rt);
-  T* row = X + a * R;
   for (uint32_t q = threadIdx.x; q < R; q += blockDim.x)
     Z[q] = q < b ? row[q] : E[q];
   __syncthreads();
@@ -375,7 +374,7 @@ struct Launch {
       const uint32_t grid =
           v2_grid(k_row_fwd2<F, LR>, Geo::THREADS, sm, P.a, Geo::G, nsm);
       TFT_LAUNCH(K_ROW_FWD, k_row_fwd2<F, LR><<<grid, Geo::THREADS, sm, s>>>(
-                                x, P.a, rt));
+                                x, P.a, 0, rt));
     });
     return cudaGetLastError();
   }
@@ -387,7 +386,7 @@ struct Launch {
       const uint32_t grid =
           v2_grid(k_row_inv2<F, LR>, Geo::THREADS, sm, P.a, Geo::G, nsm);
       TFT_LAUNCH(K_ROW_INV, k_row_inv2<F, LR><<<grid, Geo::THREADS, sm, s>>>(
-                                x, P.a, rt));
+                                x, P.a, 0, rt));
     });
     return cudaGetLastError();
   }
@@ -473,7 +472,8 @@ struct Launch {
         TFT_LAUNCH_ON(K_LASTROW_FWD, s2,
                       (k_row_last2<F, LR><<<1, Geo::THREADS,
                                             row_smem_bytes<T>(LR, Geo::G, 1),
-                                            s2>>>(x, E, P.a, P.b, rt)));
+                                            s2>>>(x + P.a * (1ull << LR), E,
+                                                  P.a, P.b, rt)));
       });
     }
     cudaError_t e = rows_fwd_v2(x, P, rt, nsm, s, H);
@@ -511,7 +511,7 @@ struct Launch {
     if (P.b > 0) {
       TFT_LAUNCH(K_LASTROW_INV,
                  k_lastrow_inv<F><<<1, 512, smem_row<F>(P.lr, 1), s>>>(
-                     x, E, P.lr, P.a, P.b, rt));
+                     x + P.a * (uint64_t)R, E, P.lr, P.a, P.b, rt));
       const uint32_t qe = (uint32_t)P.b;
       const int cl = set_clog(P, qe, nsm);
       const uint32_t C = 1u << cl;
@@ -520,6 +520,107 @@ struct Launch {
                                       col_smem_bytes<T>(P.c, cl), s>>>(
                      x, E, P.lr, (uint32_t)(P.a + 1), P.c, cl, 0, qe, 0,
                      omega_a_tw, in_scale_log, rt, ~0ull, nullptr));
+    }
+    return cudaGetLastError();
+  }
+
+  // ---- pieces of a transform held in parts (a sharded transform) ---------
+  // A part holds a block of W = 2^{Pc.lr} adjacent columns of the R-wide
+  // view, (a + 1) x W words at row stride W, and/or a run of full rows.
+  // Pc is the transform's plan with lr = log2 W and b = the block's long
+  // columns (the column transforms do not depend on which columns they
+  // are, so the block is a column pass of its own).
+  //   dir 0: forward columns, long and short, E[j] = C_j(omega_a) for the
+  //          short ones (want_E);
+  //   dir 1, which 0: inverse of the short columns (length a), with E;
+  //   dir 1, which 1: inverse of the long columns (length a + 1, row a
+  //          already holding the last row's inverse).
+  static cudaError_t shard_cols(int dir, int which, T* blk, const Plan& Pc,
+                                T* E, int want_E, T omega_a_tw, const RT& rt,
+                                int nsm, cudaStream_t s, const LaunchHook* H) {
+    const uint32_t W = 1u << Pc.lr;
+    if (dir == 0 && want_E && Pc.b == 0) {
+      // every column of the block is short but the transform has a ragged
+      // row: the column pass produces row a (C_q(omega_a), the padded
+      // transform's output there) only for long columns, so run the block
+      // as all-long columns whose row-a inputs are zero (positions >= a W
+      // read as zero) and take E from the block's row a
+      Plan P2 = Pc;
+      P2.b = W;
+      cudaError_t e = cols_fwd_v2(blk, Pc.a * (uint64_t)W, blk, nullptr, P2,
+                                  rt, nsm, s, H);
+      if (e != cudaSuccess) return e;
+      return cudaMemcpyAsync(E, blk + Pc.a * (uint64_t)W, W * sizeof(T),
+                             cudaMemcpyDeviceToDevice, s);
+    }
+    if (dir == 0)
+      return cols_fwd_v2(blk, Pc.a * (uint64_t)W + Pc.b, blk, want_E ? E
+                                                                       : nullptr,
+                         Pc, rt, nsm, s, H);
+    if (which == 0) {
+      if (Pc.a == 0 || Pc.b >= W) return cudaSuccess;
+      const uint32_t qb = (uint32_t)Pc.b;
+      const int cl = set_clog(Pc, W - qb, nsm);
+      const uint32_t C = 1u << cl;
+      TFT_LAUNCH(K_COL_INV,
+                 k_col_inv2<F, 256><<<(W - qb + C - 1) / C, 256,
+                                      col_smem_bytes<T>(Pc.c, cl), s>>>(
+                     blk, E, Pc.lr, (uint32_t)Pc.a, Pc.c, cl, qb, W, want_E,
+                     omega_a_tw, 0, rt, ~0ull, nullptr));
+      return cudaGetLastError();
+    }
+    if (Pc.b == 0) return cudaSuccess;
+    const uint32_t qe = (uint32_t)Pc.b;
+    const int cl = set_clog(Pc, qe, nsm);
+    const uint32_t C = 1u << cl;
+    TFT_LAUNCH(K_COL_INV,
+               k_col_inv2<F, 256><<<(qe + C - 1) / C, 256,
+                                    col_smem_bytes<T>(Pc.c, cl), s>>>(
+                   blk, nullptr, Pc.lr, (uint32_t)(Pc.a + 1), Pc.c, cl, 0, qe,
+                   0, omega_a_tw, 0, rt, ~0ull, nullptr));
+    return cudaGetLastError();
+  }
+  // count full rows of 2^lr words at `rows`, rows rho_off .. of the view
+  static cudaError_t shard_rows(int dir, T* rows, uint64_t count,
+                                uint64_t rho_off, int lr, const RT& rt,
+                                int nsm, cudaStream_t s, const LaunchHook* H) {
+    if (count == 0) return cudaSuccess;
+    TFT_LR_DISPATCH(lr, {
+      using Geo = RowGeom<LR, 256>;
+      const size_t sm = row_smem_bytes<T>(LR, Geo::G, 1);
+      if (dir == 0) {
+        const uint32_t grid =
+            v2_grid(k_row_fwd2<F, LR>, Geo::THREADS, sm, count, Geo::G, nsm);
+        TFT_LAUNCH(K_ROW_FWD,
+                   k_row_fwd2<F, LR><<<grid, Geo::THREADS, sm, s>>>(
+                       rows, count, rho_off, rt));
+      } else {
+        const uint32_t grid =
+            v2_grid(k_row_inv2<F, LR>, Geo::THREADS, sm, count, Geo::G, nsm);
+        TFT_LAUNCH(K_ROW_INV,
+                   k_row_inv2<F, LR><<<grid, Geo::THREADS, sm, s>>>(
+                       rows, count, rho_off, rt));
+      }
+    });
+    return cudaGetLastError();
+  }
+  // the ragged last row (row a, b outputs) from an R-word row and E
+  static cudaError_t shard_last(int dir, T* row, const T* E, uint64_t a,
+                                uint64_t b, int lr, const RT& rt,
+                                cudaStream_t s, const LaunchHook* H) {
+    if (b == 0) return cudaSuccess;
+    if (dir == 0) {
+      TFT_LR_DISPATCH(lr, {
+        using Geo = RowGeom<LR>;
+        TFT_LAUNCH(K_LASTROW_FWD,
+                   (k_row_last2<F, LR><<<1, Geo::THREADS,
+                                         row_smem_bytes<T>(LR, Geo::G, 1),
+                                         s>>>(row, E, a, b, rt)));
+      });
+    } else {
+      TFT_LAUNCH(K_LASTROW_INV,
+                 k_lastrow_inv<F><<<1, 512, smem_row<F>(lr, 1), s>>>(
+                     row, E, lr, a, b, rt));
     }
     return cudaGetLastError();
   }
@@ -925,6 +1026,27 @@ static cudaError_t launch_tail(void* X, const void* S, uint64_t Q,
                                 cudaStream_t s, const LaunchHook* hook) {     \
     return Launch<F>::inverse_zs((F::T*)x, n, P, (F::T)omega_a_tw,            \
                                  *(const RootTable<F::T>*)rt, nsm, s, hook);  \
+  }                                                                           \
+  cudaError_t NAME##_shard_cols(int dir, int which, void* blk, const Plan& Pc, \
+                                void* E, int want_E, uint64_t omega_a_tw,     \
+                                const void* rt, int nsm, cudaStream_t s,      \
+                                const LaunchHook* hook) {                     \
+    return Launch<F>::shard_cols(dir, which, (F::T*)blk, Pc, (F::T*)E,        \
+                                 want_E, (F::T)omega_a_tw,                    \
+                                 *(const RootTable<F::T>*)rt, nsm, s, hook);  \
+  }                                                                           \
+  cudaError_t NAME##_shard_rows(int dir, void* rows, uint64_t count,          \
+                                uint64_t rho_off, int lr, const void* rt,     \
+                                int nsm, cudaStream_t s,                      \
+                                const LaunchHook* hook) {                     \
+    return Launch<F>::shard_rows(dir, (F::T*)rows, count, rho_off, lr,        \
+                                 *(const RootTable<F::T>*)rt, nsm, s, hook);  \
+  }                                                                           \
+  cudaError_t NAME##_shard_last(int dir, void* row, const void* E, uint64_t a, \
+                                uint64_t b, int lr, const void* rt,           \
+                                cudaStream_t s, const LaunchHook* hook) {     \
+    return Launch<F>::shard_last(dir, (F::T*)row, (const F::T*)E, a, b, lr,   \
+                                 *(const RootTable<F::T>*)rt, s, hook);       \
   }
 
 #define TFT_DEFINE_FIELD_BATCH(F, NAME)                                       \

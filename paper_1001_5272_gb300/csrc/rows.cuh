@@ -242,18 +242,22 @@ __device__ __forceinline__ void inv_stage(typename F::T* Zrow,
   row_setup<F>(S, sp, LR, s_rt);
 
 // ---------------------------------------------------------------------------
-// Forward rows rho < a.
+// Forward rows rho < a.  The a rows at X are rows rho_off .. rho_off + a - 1
+// of the row/column view (rho_off > 0 for a block of rows held apart, as a
+// rank of a sharded transform holds them): the row factors use the global
+// row index.
 // ---------------------------------------------------------------------------
 template <class F, int LR>
 __global__ void __launch_bounds__(RowGeom<LR, 256>::THREADS, RowGeom<LR, 256>::template min_ctas<sizeof(typename F::T)>())
-k_row_fwd2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
+k_row_fwd2(typename F::T* X, uint64_t a, uint64_t rho_off,
+           RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE_G(1, RowGeom<LR, 256>)
   T* Zrow = S.Z + g * row_stride<T>(LR);
   for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
        rho0 += (uint64_t)gridDim.x * G) {
     const uint64_t rho = rho0 + g;
     const bool active = rho < a;
-    if (active) row_factors<F>(S, sp, LR, g, t, rho, s_rt);
+    if (active) row_factors<F>(S, sp, LR, g, t, rho_off + rho, s_rt);
     __syncthreads();
     T* Grow = X + rho * R;
     if (active)
@@ -276,11 +280,12 @@ k_row_fwd2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
 }
 
 // ---------------------------------------------------------------------------
-// Inverse rows rho < a.
+// Inverse rows rho < a (rows rho_off + rho of the view, as above).
 // ---------------------------------------------------------------------------
 template <class F, int LR>
 __global__ void __launch_bounds__(RowGeom<LR, 256>::THREADS, RowGeom<LR, 256>::template min_ctas<sizeof(typename F::T)>())
-k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
+k_row_inv2(typename F::T* X, uint64_t a, uint64_t rho_off,
+           RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE_G(1, RowGeom<LR, 256>)
   T* Zrow = S.Z + g * row_stride<T>(LR);
   for (uint64_t rho0 = (uint64_t)blockIdx.x * G; rho0 < a;
@@ -289,7 +294,7 @@ k_row_inv2(typename F::T* X, uint64_t a, RootTable<typename F::T> rt) {
     const bool active = rho < a;
     T* Grow = X + rho * R;
     if (active) {
-      row_factors<F>(S, sp, LR, g, t, rho, s_rt);
+      row_factors<F>(S, sp, LR, g, t, rho_off + rho, s_rt);
       // eight loads in flight per thread
       constexpr uint32_t NQ = R / Tpr;
       static_assert(NQ % 8 == 0, "row load batches of eight");
@@ -512,12 +517,11 @@ k_row_mul2(typename F::T* out, const typename F::T* __restrict__ work,
 // ---------------------------------------------------------------------------
 template <class F, int LR>
 __global__ void __launch_bounds__(RowGeom<LR>::THREADS, RowGeom<LR>::template min_ctas<sizeof(typename F::T)>())
-k_row_last2(typename F::T* X, const typename F::T* __restrict__ E,
+k_row_last2(typename F::T* GA, const typename F::T* __restrict__ E,
             uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
   TFT_ROW_PROLOGUE(1)
-  // one row: slot 0 of the first CTA
+  // one row (GA = row a of the view): slot 0 of the first CTA
   const bool active = blockIdx.x == 0 && g == 0;
-  T* GA = X + a * R;
   T* ZA = S.Z + g * row_stride<T>(LR);
   constexpr int last = Geo::NST - 1;
   if (active) {

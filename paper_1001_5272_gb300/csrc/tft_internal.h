@@ -129,6 +129,17 @@ cudaError_t launch_forward_zs(int prime, void* x, uint64_t n, const Plan& P,
 cudaError_t launch_inverse_zs(int prime, void* x, uint64_t n, const Plan& P,
                               uint64_t omega_a_tw, const void* rt, int nsm,
                               cudaStream_t s, const LaunchHook* hook);
+// Pieces of a transform held in parts (kernels_impl.cuh, Launch::shard_*).
+cudaError_t launch_shard_cols(int prime, int dir, int which, void* blk,
+                              const Plan& Pc, void* E, int want_E,
+                              uint64_t omega_a_tw, const void* rt, int nsm,
+                              cudaStream_t s, const LaunchHook* hook);
+cudaError_t launch_shard_rows(int prime, int dir, void* rows, uint64_t count,
+                              uint64_t rho_off, int lr, const void* rt,
+                              int nsm, cudaStream_t s, const LaunchHook* hook);
+cudaError_t launch_shard_last(int prime, int dir, void* row, const void* E,
+                              uint64_t a, uint64_t b, int lr, const void* rt,
+                              cudaStream_t s, const LaunchHook* hook);
 cudaError_t launch_polymul(int prime, const void* a, uint64_t na,
                            const void* b, uint64_t nb, void* out,
                            const Plan& P, void* work, void* EA, void* EB,

@@ -110,6 +110,9 @@ def load():
         "tft_forward_noalloc": (i32, [i32, vp, u64, u32, vp]),
         "tft_calibrate": (i32, [vp, i32, u32, u32, vp, u64, vp,
                                 ctypes.POINTER(u64)]),
+        "tft_shard_columns": (i32, [vp, i32, i32, vp, u64, u32, u32, vp, vp]),
+        "tft_shard_rows": (i32, [vp, i32, vp, u64, u64, u64, vp]),
+        "tft_shard_last_row": (i32, [vp, i32, vp, vp, u64, vp]),
         "tft_debug_fail_allocation": (None, [ctypes.c_int64]),
         "tft_debug_live_allocations": (ctypes.c_int64, []),
         "tft_forward_noscratch": (i32, [i32, vp, u64, u32, vp]),
@@ -406,6 +409,38 @@ def tft_profile_read(ctx):
 
 def tft_launch_count(ctx):
     return int(load().tft_launch_count(ctx.handle))
+
+
+def _opt_ptr(t, elem_bytes, what):
+    return ctypes.c_void_p(None) if t is None else _dev_ptr(t, elem_bytes,
+                                                             what)
+
+
+def tft_shard_columns(ctx, inverse, which, block, n, parts, part, E=None,
+                      stream=None):
+    """Column step of a transform of length n held in `parts` parts, on
+    part `part`'s (a + 1) x W column block (include/tft.h)."""
+    _check(load().tft_shard_columns(
+        ctx.handle, int(inverse), int(which),
+        _dev_ptr(block, ctx.elem_bytes, "block"), int(n), int(parts),
+        int(part), _opt_ptr(E, ctx.elem_bytes, "E"), _stream_handle(stream)),
+        "tft_shard_columns")
+
+
+def tft_shard_rows(ctx, inverse, rows, n, rho_begin, count, stream=None):
+    """Row step on `count` full rows (rows rho_begin.. of the view)."""
+    _check(load().tft_shard_rows(
+        ctx.handle, int(inverse),
+        _opt_ptr(rows if count else None, ctx.elem_bytes, "rows"), int(n),
+        int(rho_begin), int(count), _stream_handle(stream)), "tft_shard_rows")
+
+
+def tft_shard_last_row(ctx, inverse, row, E, n, stream=None):
+    """The ragged last row from an R-word row buffer and the R-word E."""
+    _check(load().tft_shard_last_row(
+        ctx.handle, int(inverse), _dev_ptr(row, ctx.elem_bytes, "row"),
+        _dev_ptr(E, ctx.elem_bytes, "E"), int(n), _stream_handle(stream)),
+        "tft_shard_last_row")
 
 
 def tft_debug_fail_allocation(n):
