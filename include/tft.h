@@ -464,6 +464,30 @@ const char* tft_kernel_name(int kind);
 uint64_t tft_launch_count(tft_ctx* ctx);
 
 /*
+ * tft_transform_batch: the in-place forward (inverse = 0, Algorithm 1) or
+ * inverse (inverse = 1, Algorithm 2) TFT of every buffer of a batch of
+ * uneven lengths -- results bit for bit those of tft_forward / tft_inverse
+ * on each buffer alone.  The transforms short enough for one CTA (2^12
+ * words for 2^64 - 2^32 + 1, 2^13 otherwise) run in one persistent launch,
+ * one CTA per transform at a time; the longer ones follow one after another
+ * on `stream` on the row/column path (they share the context's scratch).
+ *   descs   count entries {x, n}: 16-byte aligned device buffers that do
+ *           not overlap, 1 <= n <= the context's max_len
+ * The table of the short transforms goes into the context's batch
+ * reservation (tft_ctx_reserve_batch with at least that many products;
+ * work_words may be 0) and replaces a product batch planned there.
+ * Errors: TFT_EINVAL for a null, misaligned or overlapping buffer or n = 0;
+ * TFT_ERANGE for n beyond max_len or a reservation too small.
+ */
+typedef struct tft_transform_desc {
+  void* x;
+  uint64_t n;
+} tft_transform_desc;
+tft_status tft_transform_batch(tft_ctx* ctx, int inverse,
+                               const tft_transform_desc* descs,
+                               uint32_t count, void* stream);
+
+/*
  * Pieces of a transform held in parts -- the data plane of a transform
  * sharded over several GPUs (one part per rank).  The library's transforms
  * of length n = a R + b (R = 2^lr, the split tft_describe_plan reports;

@@ -557,6 +557,72 @@ tft_status tft_inverse(tft_ctx* ctx, void* X, uint64_t n, uint32_t k,
                                        (cudaStream_t)stream, &ctx->hook));
 }
 
+tft_status tft_transform_batch(tft_ctx* ctx, int inverse,
+                               const tft_transform_desc* descs,
+                               uint32_t count, void* stream) {
+  if (!ctx || (!descs && count)) return TFT_EINVAL;
+  if (count == 0) return TFT_OK;
+  const size_t w = ctx->pr.w;
+  std::vector<XformDesc> small;
+  std::vector<std::pair<uintptr_t, uint64_t>> spans;
+  small.reserve(count);
+  spans.reserve(count);
+  int lmax = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    const tft_transform_desc& d = descs[i];
+    if (!d.x || d.n == 0 || !aligned16(d.x)) return TFT_EINVAL;
+    if (d.n > ctx->max_len) return TFT_ERANGE;
+    Plan P;
+    if (!make_plan(ctx->prime, d.n, &P)) return TFT_ERANGE;
+    spans.push_back({(uintptr_t)d.x, d.n * w});
+    if (P.small) {
+      small.push_back(XformDesc{(uint64_t)d.x, (uint32_t)d.n, (uint32_t)P.l});
+      if (P.l > lmax) lmax = P.l;
+    }
+  }
+  // the buffers must not overlap (each is transformed in place)
+  std::sort(spans.begin(), spans.end());
+  for (size_t i = 1; i < spans.size(); ++i)
+    if (spans[i - 1].first + spans[i - 1].second > spans[i].first)
+      return TFT_EINVAL;
+  if (!small.empty() &&
+      (!ctx->batch_tab || small.size() > ctx->batch_max ||
+       small.size() * sizeof(XformDesc) > ctx->batch_tab_bytes))
+    return TFT_ERANGE;
+  DeviceGuard g(ctx->device);
+  if (!g.ok) return TFT_ECUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!small.empty()) {
+    // the table goes into the batch reservation (a product plan there is
+    // dropped); pageable source: the copy is staged before the call returns
+    ctx->batch_ready = 0;
+    cudaError_t e = cudaMemcpyAsync(ctx->batch_tab, small.data(),
+                                    small.size() * sizeof(XformDesc),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = launch_small_batch(ctx->prime, ctx->batch_tab,
+                             (uint32_t)small.size(), lmax, inverse ? 1 : 0,
+                             ctx->rt, ctx->nsm, s, &ctx->hook);
+    if (e != cudaSuccess) return from_cuda(ctx, e);
+  }
+  // the longer transforms one after another on the stream (they share the
+  // context's scratch)
+  for (uint32_t i = 0; i < count; ++i) {
+    const tft_transform_desc& d = descs[i];
+    Plan P;
+    make_plan(ctx->prime, d.n, &P);
+    if (P.small) continue;
+    cudaError_t e =
+        inverse ? launch_inverse(ctx->prime, d.x, d.n, P, ctx->scratch,
+                                 omega_a_tw(ctx, P), ctx->rt, ctx->nsm, s,
+                                 &ctx->hook)
+                : launch_forward(ctx->prime, d.x, d.n, P, ctx->scratch,
+                                 ctx->rt, ctx->nsm, s, &ctx->hook, &ctx->aux);
+    if (e != cudaSuccess) return from_cuda(ctx, e);
+  }
+  return TFT_OK;
+}
+
 // The plan of a transform of length n held in `parts` parts, and the
 // column block plan of part `part` (row stride W = R / parts, b = the
 // block's long columns).

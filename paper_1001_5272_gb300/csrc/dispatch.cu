@@ -24,6 +24,9 @@ namespace tftgb {
   cudaError_t NAME##_inverse_zs(void* x, uint64_t n, const Plan& P,           \
                                 uint64_t omega_a_tw, const void* rt, int nsm, \
                                 cudaStream_t s, const LaunchHook* hook);      \
+  cudaError_t NAME##_small_batch(const void* d, uint32_t count, int lmax,     \
+                                 int inverse, const void* rt, int nsm,        \
+                                 cudaStream_t s, const LaunchHook* hook);     \
   cudaError_t NAME##_shard_cols(int dir, int which, void* blk, const Plan& Pc, \
                                 void* E, int want_E, uint64_t omega_a_tw,     \
                                 const void* rt, int nsm, cudaStream_t s,      \
@@ -158,6 +161,15 @@ cudaError_t launch_tail(int prime, void* X, const void* S, uint64_t Q,
   TFT_BY_PRIME(prime, p998_tail(X, S, Q, lo, hi, mul, nsm, s),
                p2013_tail(X, S, Q, lo, hi, mul, nsm, s),
                gold_tail(X, S, Q, lo, hi, mul, nsm, s));
+}
+
+cudaError_t launch_small_batch(int prime, const void* d, uint32_t count,
+                               int lmax, int inverse, const void* rt, int nsm,
+                               cudaStream_t s, const LaunchHook* hook) {
+  TFT_BY_PRIME(prime,
+               p998_small_batch(d, count, lmax, inverse, rt, nsm, s, hook),
+               p2013_small_batch(d, count, lmax, inverse, rt, nsm, s, hook),
+               gold_small_batch(d, count, lmax, inverse, rt, nsm, s, hook));
 }
 
 cudaError_t launch_shard_cols(int prime, int dir, int which, void* blk,

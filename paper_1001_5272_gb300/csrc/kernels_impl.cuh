@@ -250,6 +250,41 @@ k_row_mul(typename F::T* out, const typename F::T* __restrict__ work,
   }
 }
 
+// Many single-CTA transforms of uneven lengths in one launch: each CTA
+// takes table entries blockIdx.x, blockIdx.x + gridDim.x, ... and runs the
+// whole transform of each (the k_small body) in shared memory sized for
+// the largest.
+template <class F, bool INV>
+__global__ void __launch_bounds__(512)
+k_small_batch(const XformDesc* __restrict__ d, uint32_t count,
+              RootTable<typename F::T> rt) {
+  using T = typename F::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<T> s_rt;
+  load_roots<F>(&s_rt, rt);
+  T* Z = reinterpret_cast<T*>(smem_raw);
+  for (uint32_t p = blockIdx.x; p < count; p += gridDim.x) {
+    const XformDesc q = d[p];
+    const int l = (int)q.l;
+    const uint32_t N = 1u << l, n = q.n;
+    T* x = reinterpret_cast<T*>(q.x);
+    T* W = Z + N;
+    T* Wih = W + (N > 1 ? N / 2 : 1);
+    __syncthreads();  // the previous transform is done with shared memory
+    build_base_tables<F>(W, INV ? Wih : nullptr, l, s_rt);
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x)
+      Z[i] = i < n ? x[i] : T(0);
+    __syncthreads();
+    ColTw<F> tw{W, Wih};
+    if (!INV)
+      fwd_pruned<F>(Z, 0, 0, l, n, tw);
+    else
+      inv_block<F>(Z, 0, 0, l, n, tw);
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+      x[i] = F::canon(Z[i]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host launchers
 // ---------------------------------------------------------------------------
@@ -331,6 +366,8 @@ struct Launch {
 
     if ((e = set_smem<F>((const void*)k_small<F, false>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_small<F, true>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_small_batch<F, false>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_small_batch<F, true>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_small_mul<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_row_fwd<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_row_inv<F>, mx))) return e;
@@ -520,6 +557,25 @@ struct Launch {
                                       col_smem_bytes<T>(P.c, cl), s>>>(
                      x, E, P.lr, (uint32_t)(P.a + 1), P.c, cl, 0, qe, 0,
                      omega_a_tw, in_scale_log, rt, ~0ull, nullptr));
+    }
+    return cudaGetLastError();
+  }
+
+  static cudaError_t small_batch(const XformDesc* d, uint32_t count, int lmax,
+                                 bool inv, const RT& rt, int nsm,
+                                 cudaStream_t s, const LaunchHook* H) {
+    if (count == 0) return cudaSuccess;
+    const size_t sm = smem_small<F>(lmax, inv);
+    if (inv) {
+      const uint32_t grid =
+          persistent_grid(k_small_batch<F, true>, 512, sm, count, nsm);
+      TFT_LAUNCH(K_SMALL,
+                 k_small_batch<F, true><<<grid, 512, sm, s>>>(d, count, rt));
+    } else {
+      const uint32_t grid =
+          persistent_grid(k_small_batch<F, false>, 512, sm, count, nsm);
+      TFT_LAUNCH(K_SMALL,
+                 k_small_batch<F, false><<<grid, 512, sm, s>>>(d, count, rt));
     }
     return cudaGetLastError();
   }
@@ -1026,6 +1082,13 @@ static cudaError_t launch_tail(void* X, const void* S, uint64_t Q,
                                 cudaStream_t s, const LaunchHook* hook) {     \
     return Launch<F>::inverse_zs((F::T*)x, n, P, (F::T)omega_a_tw,            \
                                  *(const RootTable<F::T>*)rt, nsm, s, hook);  \
+  }                                                                           \
+  cudaError_t NAME##_small_batch(const void* d, uint32_t count, int lmax,     \
+                                 int inverse, const void* rt, int nsm,        \
+                                 cudaStream_t s, const LaunchHook* hook) {    \
+    return Launch<F>::small_batch((const XformDesc*)d, count, lmax,           \
+                                  inverse != 0, *(const RootTable<F::T>*)rt,  \
+                                  nsm, s, hook);                              \
   }                                                                           \
   cudaError_t NAME##_shard_cols(int dir, int which, void* blk, const Plan& Pc, \
                                 void* E, int want_E, uint64_t omega_a_tw,     \

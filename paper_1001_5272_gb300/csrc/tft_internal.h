@@ -64,6 +64,13 @@ struct AuxStreams {
   cudaEvent_t join;
 };
 
+// One transform of a batch of single-CTA transforms (device table entry).
+struct XformDesc {
+  uint64_t x;  // device pointer
+  uint32_t n;  // length
+  uint32_t l;  // padded length 2^l >= n
+};
+
 // A planned batch of products (tables already on the device).
 struct BatchLaunch {
   const void* small;   // BatchSmall[ns] on the device
@@ -129,6 +136,11 @@ cudaError_t launch_forward_zs(int prime, void* x, uint64_t n, const Plan& P,
 cudaError_t launch_inverse_zs(int prime, void* x, uint64_t n, const Plan& P,
                               uint64_t omega_a_tw, const void* rt, int nsm,
                               cudaStream_t s, const LaunchHook* hook);
+// Single-CTA transforms of a batch, one persistent launch (lmax: the
+// largest l of the table).
+cudaError_t launch_small_batch(int prime, const void* d, uint32_t count,
+                               int lmax, int inverse, const void* rt, int nsm,
+                               cudaStream_t s, const LaunchHook* hook);
 // Pieces of a transform held in parts (kernels_impl.cuh, Launch::shard_*).
 cudaError_t launch_shard_cols(int prime, int dir, int which, void* blk,
                               const Plan& Pc, void* E, int want_E,

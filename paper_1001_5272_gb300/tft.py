@@ -36,6 +36,11 @@ class PolymulDesc(ctypes.Structure):
                 ("out", ctypes.c_void_p)]
 
 
+class TransformDesc(ctypes.Structure):
+    """tft_transform_desc."""
+    _fields_ = [("x", ctypes.c_void_p), ("n", ctypes.c_uint64)]
+
+
 class BatchParams(ctypes.Structure):
     """tft_batch_params: 0 in a field selects the library default."""
     _fields_ = [("small_log", ctypes.c_uint32), ("lr", ctypes.c_uint32),
@@ -110,6 +115,8 @@ def load():
         "tft_forward_noalloc": (i32, [i32, vp, u64, u32, vp]),
         "tft_calibrate": (i32, [vp, i32, u32, u32, vp, u64, vp,
                                 ctypes.POINTER(u64)]),
+        "tft_transform_batch": (i32, [vp, i32, ctypes.POINTER(TransformDesc),
+                                      u32, vp]),
         "tft_shard_columns": (i32, [vp, i32, i32, vp, u64, u32, u32, vp, vp]),
         "tft_shard_rows": (i32, [vp, i32, vp, u64, u64, u64, vp]),
         "tft_shard_last_row": (i32, [vp, i32, vp, vp, u64, vp]),
@@ -538,6 +545,17 @@ def _params(params):
     clog = params.get("clog")
     p.clog_plus1 = 0 if clog is None else int(clog) + 1
     return ctypes.byref(p)
+
+
+def tft_transform_batch(ctx, xs, inverse=False, stream=None):
+    """In-place forward (or inverse) TFT of every CUDA tensor in xs."""
+    arr = (TransformDesc * max(1, len(xs)))()
+    for i, x in enumerate(xs):
+        arr[i].x = _dev_ptr(x, ctx.elem_bytes, "x").value
+        arr[i].n = x.numel()
+    _check(load().tft_transform_batch(ctx.handle, 1 if inverse else 0, arr,
+                                      len(xs), _stream_handle(stream)),
+           "tft_transform_batch")
 
 
 def tft_ctx_reserve_batch(ctx, max_products, work_words):
