@@ -683,6 +683,8 @@ def run_ours(args):
 
         extra["batched_p2013265921_4096"] = batched_leg(args, tft, dev,
                                                         steps)
+        extra["transform_batch_p2013265921_4096"] = transform_batch_leg(
+            args, tft, dev, steps)
         extra["calibration"] = calibration_leg(args, tft, dev)
         extra["served_goldilocks_20000rps"] = served_leg(args, tft, dev)
 
@@ -849,6 +851,54 @@ def batched_leg(args, tft, dev, steps):
             "graph": "all launches of one batch captured in one CUDA graph",
             "kernels_ms": {k: v[0] for k, v in prof.items()},
             "matches_single_calls": ok}
+
+
+def transform_batch_leg(args, tft, dev, steps):
+    """4096 forward TFTs over 2013265921 of lengths log-uniform in
+    [64, 65536] (the batched workload's a-operand lengths) through
+    tft_transform_batch, against the same transforms one call at a time;
+    Sum n / time, CUDA events around each."""
+    import numpy as np
+    import torch
+
+    from workloads import config4_inputs
+
+    A, _ = config4_inputs(args.batch_count)
+    n = np.array([a.size for a in A])
+    buf, off = pack_aligned([a.astype(np.uint32) for a in A], 4)
+    x0 = torch.from_numpy(buf.view(np.int32)).to(dev)
+    x = x0.clone()
+    xs = [x[off[i]:off[i] + n[i]] for i in range(len(A))]
+    cur = torch.cuda.current_stream()
+    out = {}
+    with tft.Context(1, dev, max_len=int(n.max())) as ctx:
+        tft.tft_ctx_reserve_batch(ctx, len(A), 0)
+        for mode in ("batched", "one_by_one"):
+            ts = []
+            for rep in range(2 + max(1, min(3, steps))):
+                x.copy_(x0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(cur)
+                if mode == "batched":
+                    tft.tft_transform_batch(ctx, xs, stream=cur)
+                else:
+                    for t in xs:
+                        tft.tft_forward(ctx, t, stream=cur)
+                e1.record(cur)
+                torch.cuda.synchronize()
+                if rep >= 2:
+                    ts.append(e0.elapsed_time(e1))
+            out[mode] = {"ms": statistics.mean(ts),
+                         "mcoeffs": int(n.sum()) / statistics.mean(ts) / 1e3}
+            if mode == "batched":
+                res = x.clone()
+        out["equal"] = bool(torch.equal(res, x))
+    out["transforms"] = len(A)
+    out["sum_n"] = int(n.sum())
+    out["batched_over_one_by_one"] = (out["one_by_one"]["ms"] /
+                                      out["batched"]["ms"])
+    return out
 
 
 def restricted_leg(args, tft, dev, steps):
