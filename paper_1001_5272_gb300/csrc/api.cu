@@ -152,8 +152,25 @@ bool check_constants() {
            r2 == (uint32_t)(((u128)1 << 64) % p) &&
            one == (uint32_t)(((uint64_t)1 << 32) % p);
   };
-  return chk(P998::P, P998::PINV, P998::R2, P998::ONE) &&
-         chk(P2013::P, P2013::PINV, P2013::R2, P2013::ONE);
+  if (!chk(P998::P, P998::PINV, P998::R2, P998::ONE) ||
+      !chk(P2013::P, P2013::PINV, P2013::R2, P2013::ONE))
+    return false;
+  // the 16-point network's constants of 2^64 - 2^32 + 1 that the kernels
+  // apply as +-2^s by shifts must be the root table's omega_{2k} (and their
+  // inverses)
+  const PrimeInfo& g = kPrimes[2];
+  for (int k = 1; k < 8; ++k) {
+    const uint64_t c = omega_s(g, 2 * k);
+    const uint64_t ci = powm(c, g.p - 2, g.p);
+    for (int inv = 0; inv < 2; ++inv) {
+      const int sh = inv ? Goldilocks::kNetInvShift[k] : Goldilocks::kNetShift[k];
+      if (sh == 0) continue;
+      const uint64_t v = powm(2, (uint64_t)sh, g.p);
+      const uint64_t want = Goldilocks::net_neg(k, inv != 0) ? g.p - v : v;
+      if ((inv ? ci : c) != want) return false;
+    }
+  }
+  return true;
 }
 
 std::mutex g_prep_mu;

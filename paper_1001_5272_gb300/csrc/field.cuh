@@ -151,6 +151,36 @@ struct Goldilocks {
     return reduce128(a * b, __umul64hi(a, b));
   }
   static __device__ __forceinline__ T mul_tw(T a, T w) { return mul(a, w); }
+  // x 2^S for 0 < S < 64: the 128-bit product is (x << S, x >> (64 - S)),
+  // reduced without a multiplication.
+  template <int S>
+  static __device__ __forceinline__ T mul_pow2(T x) {
+    return reduce128(x << S, x >> (64 - S));
+  }
+  // The constants of the 16-point network, omega_{2k} for k < 8, are powers
+  // of 2 under the library's root convention (omega_[32] = 7^((p-1)/2^32)):
+  // omega_{2k} = 2^{e_k}, e = 0, 48, 120, 168, 156, 12, 84, 132 (mod 192,
+  // 2^96 = -1), i.e. +-2^s with s < 96; so are their inverses.  Where
+  // s < 64 the network multiplies by a shift and a reduction (no 64 x 64
+  // product, which would load the multiply pipe); kNet*Shift = 0 means the
+  // ordinary multiply by the table's constant, and kNet*Neg that the
+  // constant is -2^s, so the caller exchanges the sum and the difference.
+  // (The host checks these against the root table, check_constants.)
+  static constexpr int kNetShift[8] = {0, 48, 24, 0, 60, 12, 0, 36};
+  static constexpr int kNetInvShift[8] = {0, 48, 0, 24, 36, 0, 12, 60};
+  static constexpr unsigned kNetNegMask = 0x94;     // k = 2, 4, 7: -2^s
+  static constexpr unsigned kNetInvNegMask = 0x42;  // k = 1, 6
+  template <int Kk, bool INV>
+  static __device__ __forceinline__ T net_mul(T w, T c) {
+    constexpr int sh = INV ? kNetInvShift[Kk] : kNetShift[Kk];
+    if constexpr (sh > 0)
+      return mul_pow2<sh>(w);
+    else
+      return mul(w, c);
+  }
+  static __host__ __device__ constexpr bool net_neg(int k, bool inv) {
+    return (((inv ? kNetInvNegMask : kNetNegMask) >> k) & 1u) != 0;
+  }
   static __device__ __forceinline__ T mul_data(T a, T b) { return mul(a, b); }
   // a / 2 for any a < 2^64: (a - 1) / 2 + (p + 1) / 2 = (a + p) / 2 < 2^64
   // when a is odd.
@@ -196,6 +226,14 @@ struct Mont32 {
   static TFT_HD T canon_fast(T a) { return a; }
   static TFT_HD T add_c(T a, T b) { return add(a, b); }
   static TFT_HD T sub_c(T a, T b) { return sub(a, b); }
+  // the 16-point network multiplies by the table's constants here
+  template <int Kk, bool INV>
+  static __device__ __forceinline__ T net_mul(T w, T c) {
+    return mul_tw(w, c);
+  }
+  static __host__ __device__ constexpr bool net_neg(int, bool) {
+    return false;
+  }
   static TFT_HD T one_tw() { return ONE; }
 };
 

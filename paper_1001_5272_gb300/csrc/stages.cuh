@@ -169,12 +169,29 @@ __device__ __forceinline__ void powers(typename F::T (&pw)[1 << L],
                     : F::mul_tw(pw[i / 2], pw[i / 2]);
 }
 
+// The network constant's multiply for a runtime k folded to a compile-time
+// one (the networks' loops are unrolled, so k is a constant per butterfly).
+template <class F, bool INV>
+__device__ __forceinline__ typename F::T net_mul_k(int k, typename F::T w,
+                                                   typename F::T c) {
+  switch (k) {
+    case 1: return F::template net_mul<1, INV>(w, c);
+    case 2: return F::template net_mul<2, INV>(w, c);
+    case 3: return F::template net_mul<3, INV>(w, c);
+    case 4: return F::template net_mul<4, INV>(w, c);
+    case 5: return F::template net_mul<5, INV>(w, c);
+    case 6: return F::template net_mul<6, INV>(w, c);
+    default: return F::template net_mul<7, INV>(w, c);
+  }
+}
+
 // TOPCOPY: the upper half of the unit's inputs is known to be zero, so the
 // top level's butterflies (u, 0) -> (u, u) are copies.  Each butterfly
 // brings its second term m (a product, or for k = 0 the entry itself) to
 // [0, p) first, so that the sum and the difference need a single carry
 // correction (F::add_c, F::sub_c); for the 32-bit fields these are the
-// plain operations.
+// plain operations.  A constant -2^s (F::net_neg) exchanges the sum and
+// the difference.
 template <class F, int L, bool TOPCOPY = false>
 __device__ __forceinline__ void cnet_fwd(typename F::T (&x)[1 << L],
                                          const StageConsts<typename F::T>& K) {
@@ -190,16 +207,23 @@ __device__ __forceinline__ void cnet_fwd(typename F::T (&x)[1 << L],
       }
       const int k = i >> (d + 1);
       const T w = x[i + (1 << d)];
-      const T m = F::canon_fast(k == 0 ? w : F::mul_tw(w, K.c[k]));
+      const T m =
+          F::canon_fast(k == 0 ? w : net_mul_k<F, false>(k, w, K.c[k]));
       const T u = x[i];
-      x[i] = F::add_c(u, m);
-      x[i + (1 << d)] = F::sub_c(u, m);
+      if (k != 0 && F::net_neg(k, false)) {
+        x[i] = F::sub_c(u, m);
+        x[i + (1 << d)] = F::add_c(u, m);
+      } else {
+        x[i] = F::add_c(u, m);
+        x[i + (1 << d)] = F::sub_c(u, m);
+      }
     }
   }
 }
 
 // Inverse constant network without the halvings: returns 2^L times the
-// inputs of cnet_fwd.
+// inputs of cnet_fwd.  For a constant -2^s the difference is taken the
+// other way round, Y - X.
 template <class F, int L>
 __device__ __forceinline__ void cnet_inv2(typename F::T (&x)[1 << L],
                                           const StageConsts<typename F::T>& K) {
@@ -212,8 +236,13 @@ __device__ __forceinline__ void cnet_inv2(typename F::T (&x)[1 << L],
       const int k = i >> (d + 1);
       const T X = x[i], Y = F::canon_fast(x[i + (1 << d)]);
       x[i] = F::add_c(X, Y);
-      const T df = F::sub_c(X, Y);
-      x[i + (1 << d)] = k == 0 ? df : F::mul_tw(df, K.cu[k]);
+      if (k == 0) {
+        x[i + (1 << d)] = F::sub_c(X, Y);
+      } else if (F::net_neg(k, true)) {
+        x[i + (1 << d)] = net_mul_k<F, true>(k, F::sub(Y, X), K.cu[k]);
+      } else {
+        x[i + (1 << d)] = net_mul_k<F, true>(k, F::sub_c(X, Y), K.cu[k]);
+      }
     }
   }
 }
