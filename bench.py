@@ -572,6 +572,37 @@ def run_ours(args):
             "device_bytes_beyond_x": 0,
             "roundtrip_identity": bool(torch.equal(x, x0))}
         del x0
+        # the scratch-free transforms where the ragged row is one word
+        # (b = 1: the cluster evaluates E_q over nearly every column), for
+        # 2^64 - 2^32 + 1 and for 2013265921 near its largest length
+        sweep = []
+        for pid, nn in ((2, (1 << 24) + 1), (1, (1 << 27) - (1 << 14) + 1)):
+            pl = tft.tft_describe_plan(pid, nn)
+            with tft.Context(pid, dev, max_len=nn) as cz:
+                xz = torch.zeros(nn, dtype=torch.int64 if pid == 2
+                                 else torch.int32, device=dev)
+                t = {}
+                for name, fn in (
+                        ("forward_ms", lambda: tft.tft_forward(cz, xz)),
+                        ("inverse_ms", lambda: tft.tft_inverse(cz, xz)),
+                        ("forward_noscratch_ms",
+                         lambda: tft.tft_forward_noscratch(pid, xz)),
+                        ("inverse_noscratch_ms",
+                         lambda: tft.tft_inverse_noscratch(pid, xz))):
+                    fn()
+                    ts = []
+                    for _ in range(3):
+                        flush.zero_()
+                        ev[0].record(stream)
+                        fn()
+                        ev[1].record(stream)
+                        torch.cuda.synchronize()
+                        ts.append(ev[0].elapsed_time(ev[1]))
+                    t[name] = statistics.median(ts)
+                del xz
+            sweep.append({"prime": pid, "n": nn, "a": pl["a"], "b": pl["b"],
+                          "lr": pl["lr"], **t})
+        extra["tft_n17838137_noscratch"]["ragged_row_of_one"] = sweep
         # ---- the space-restricted product (Algorithm 3) -------------------
         out_r = torch.empty(R_PROD, dtype=torch.int64, device=dev)
         for _ in range(2):
