@@ -214,12 +214,15 @@ typedef struct tft_polymul_desc {
 /* Batch schedule; 0 in a field means the default (32-bit primes:
  * small_log 13, lr 9, 16 columns per tile; 2^64 - 2^32 + 1: 12, 10, 4).
  * Constraints: 8 <= lr <= 12, lr <= small_log <= 13 (12 for 64-bit
- * elements), columns per tile 2^(clog_plus1 - 1) <= 32. */
+ * elements), columns per tile 2^(clog_plus1 - 1) <= 32.  clog_lo_plus1:
+ * the column tile width of the size class whose columns are shorter than
+ * the batch's tallest (its column passes run as launches of their own),
+ * 2^(clog_lo_plus1 - 1) <= 32 columns; 0 = the same as clog_plus1. */
 typedef struct tft_batch_params {
   uint32_t small_log;
   uint32_t lr;
   uint32_t clog_plus1;
-  uint32_t reserved;
+  uint32_t clog_lo_plus1;
 } tft_batch_params;
 
 tft_status tft_ctx_reserve_batch(tft_ctx* ctx, uint32_t max_products,

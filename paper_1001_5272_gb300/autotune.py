@@ -2,7 +2,9 @@
 
 A batch is split into two size classes at r = 2^small_log: the single-CTA
 class below, the row/column class (one row length 2^lr, 2^clog columns per
-column tile) above.  The best split and row geometry depend on the batch's
+column tile) above; within the row/column class the products whose columns
+are shorter than the tallest get a column tile width of their own
+(clog_lo), tuned after the rest.  The best split and row geometry depend on the batch's
 length mix and on the device, so ``tune_batch`` times every admissible
 schedule from a small candidate grid on the batch itself (plan once per
 candidate, then CUDA-event timed runs) and returns the fastest.  Results
@@ -70,6 +72,19 @@ def _store_cache(c):
         pass
 
 
+def _column_classes(lengths, params):
+    """Distinct column heights (padded, log2) among the products that take
+    the row/column path under ``params``."""
+    cs = set()
+    for na, nb in lengths:
+        r = int(na) + int(nb) - 1
+        if r <= (1 << params["small_log"]):
+            continue
+        rows = -(-r // (1 << params["lr"]))
+        cs.add((rows - 1).bit_length())
+    return len(cs)
+
+
 def time_schedule(ctx, products, params, reps=3, stream=None):
     """Mean milliseconds of one tft_batch_run of ``products`` planned with
     ``params`` (the batch reservation must already cover them)."""
@@ -116,6 +131,23 @@ def tune_batch(ctx, products, reps=3, use_cache=True, grid=None):
             best, best_ms = g, ms
     if best is None:
         raise RuntimeError("no admissible batch schedule")
+    # per size class: when the row/column products have columns of more
+    # than one height, the shorter-column class runs its column passes as
+    # launches of their own, and its tile width is tuned separately
+    if _column_classes(lengths, best) > 1:
+        for cl in range(0, min(5, best["lr"]) + 1):
+            if cl == best["clog"]:
+                continue
+            g = dict(best, clog_lo=cl)
+            try:
+                ms = time_schedule(ctx, products, g, reps)
+            except tft.TFTError as e:
+                if e.status != tft.TFT_ERANGE:
+                    raise
+                continue
+            table["s{small_log}-lr{lr}-c{clog}-clo{clog_lo}".format(**g)] = ms
+            if ms < best_ms:
+                best, best_ms = g, ms
     if use_cache:
         c = _load_cache()
         c[key] = {"params": best, "ms": best_ms, "table": table}

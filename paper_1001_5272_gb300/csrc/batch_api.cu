@@ -18,12 +18,13 @@ BatchSchedule batch_schedule(const PrimeInfo& pr,
                              const tft_batch_params* params) {
   // small class in one CTA up to 2^13 words (u32) / 2^12 (u64); the large
   // class on rows of 2^9 (u32) / 2^10 (u64) with 16 / 4 columns per tile
-  BatchSchedule S = pr.w == 8 ? BatchSchedule{12, 10, 2}
-                              : BatchSchedule{13, 9, 4};
+  BatchSchedule S = pr.w == 8 ? BatchSchedule{12, 10, 2, -1}
+                              : BatchSchedule{13, 9, 4, -1};
   if (params) {
     if (params->small_log) S.small_log = (int)params->small_log;
     if (params->lr) S.lr = (int)params->lr;
     if (params->clog_plus1) S.clog = (int)params->clog_plus1 - 1;
+    if (params->clog_lo_plus1) S.clog_lo = (int)params->clog_lo_plus1 - 1;
   }
   return S;
 }
@@ -32,7 +33,8 @@ bool batch_schedule_valid(const PrimeInfo& pr, const BatchSchedule& S) {
   const int small_max = pr.w == 8 ? 12 : 13;
   return S.lr >= 8 && S.lr <= 12 && S.small_log >= S.lr &&
          S.small_log <= small_max && S.clog >= 0 && S.clog <= 5 &&
-         S.clog <= S.lr;
+         S.clog <= S.lr && S.clog_lo >= -1 && S.clog_lo <= 5 &&
+         S.clog_lo <= S.lr;
 }
 
 uint64_t batch_product_work_words(const PrimeInfo& pr, const BatchSchedule& S,
@@ -139,6 +141,12 @@ tft_status batch_describe(const PrimeInfo& pr, const BatchSchedule& S,
       ++nl_lo;
       cmax_lo = std::max(cmax_lo, (int)q.c);
     }
+  // the shorter-column class's tiles with their own width must fit too
+  if (nl_lo > 0 && S.clog_lo >= 0) {
+    const size_t need = w == 8 ? col_smem_bytes<uint64_t>(cmax_lo, S.clog_lo)
+                               : col_smem_bytes<uint32_t>(cmax_lo, S.clog_lo);
+    if (need + sizeof(RootTable<uint64_t>) + 256 > optin) return TFT_ERANGE;
+  }
   // rows a_p (+ the full row a_p when b_p > 0); all R columns inverted,
   // R / C tiles per product
   uint64_t rows_acc = 0;
@@ -153,6 +161,7 @@ tft_status batch_describe(const PrimeInfo& pr, const BatchSchedule& S,
   B->lmax = lmax;
   B->lr = S.lr;
   B->clog = S.clog;
+  B->clog_lo = S.clog_lo >= 0 ? S.clog_lo : S.clog;
   B->cmax = cmax;
   B->nl_lo = nl_lo;
   B->cmax_lo = cmax_lo;

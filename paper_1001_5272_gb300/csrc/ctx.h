@@ -85,6 +85,7 @@ bool make_plan(int prime, uint64_t n, Plan* out);
 // Batch schedule with the library defaults filled in.
 struct BatchSchedule {
   int small_log, lr, clog;
+  int clog_lo;  // tile width of the shorter-column class; -1: clog
 };
 BatchSchedule batch_schedule(const PrimeInfo& pr,
                              const tft_batch_params* params);

@@ -900,43 +900,46 @@ struct Launch {
     if (B.nl) {
       const BatchLarge* d = (const BatchLarge*)B.large;
       const uint32_t R = 1u << B.lr;
-      const uint32_t tiles = R >> B.clog;
       const size_t smc = col_smem_bytes<T>(B.cmax, B.clog);
       // the products are sorted by column height: when the shorter ones'
       // tiles let more CTAs reside per SM, their column passes run as a
       // launch of their own with the smaller tiles
+      // a schedule may give that class its own tile width (clog_lo)
       uint32_t nlo = 0;
       size_t smlo = smc;
       if (B.nl_lo > 0 && B.nl_lo < B.nl) {
-        const size_t sm1 = col_smem_bytes<T>(B.cmax_lo, B.clog);
+        const size_t sm1 = col_smem_bytes<T>(B.cmax_lo, B.clog_lo);
         int o0 = 0, o1 = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &o0, k_col_fwd_batch<F>, 256, smc) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &o1, k_col_fwd_batch<F>, 256, sm1) == cudaSuccess &&
-            o1 > o0) {
+        if (B.clog_lo != B.clog ||
+            (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                 &o0, k_col_fwd_batch<F>, 256, smc) == cudaSuccess &&
+             cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                 &o1, k_col_fwd_batch<F>, 256, sm1) == cudaSuccess &&
+             o1 > o0)) {
           nlo = B.nl_lo;
           smlo = sm1;
         }
       }
-      auto col_fwd = [&](const BatchLarge* dd, uint32_t np, size_t sm) {
-        const uint64_t tasks = (uint64_t)np * 2 * tiles;
+      auto col_fwd = [&](const BatchLarge* dd, uint32_t np, size_t sm,
+                         int cl) {
+        const uint64_t tasks = (uint64_t)np * 2 * (R >> cl);
         TFT_LAUNCH(K_COL_FWD,
                    (k_col_fwd_batch<F><<<persistent_grid(k_col_fwd_batch<F>,
                                                          256, sm, tasks, nsm),
-                                         256, sm, s>>>(dd, np, B.lr, B.clog,
+                                         256, sm, s>>>(dd, np, B.lr, cl,
                                                        rt)));
       };
-      auto col_inv = [&](const BatchLarge* dd, uint32_t np, size_t sm) {
-        const uint64_t tasks = (uint64_t)np * tiles;
+      auto col_inv = [&](const BatchLarge* dd, uint32_t np, size_t sm,
+                         int cl) {
+        const uint64_t tasks = (uint64_t)np * (R >> cl);
         TFT_LAUNCH(K_COL_INV,
                    (k_col_inv_batch<F><<<persistent_grid(k_col_inv_batch<F>,
                                                          256, sm, tasks, nsm),
                                          256, sm, s>>>(dd, np, tasks, B.lr,
-                                                       B.clog, rt)));
+                                                       cl, rt)));
       };
-      if (nlo) col_fwd(d, nlo, smlo);
-      col_fwd(d + nlo, B.nl - nlo, smc);
+      if (nlo) col_fwd(d, nlo, smlo, B.clog_lo);
+      col_fwd(d + nlo, B.nl - nlo, smc, B.clog);
       TFT_LR_DISPATCH_BATCH(B.lr, {
         using Geo = RowGeom<LR>;
         // the row prefix goes to shared memory when its values fit 32 bits
@@ -963,8 +966,8 @@ struct Launch {
                                              Geo::THREADS, smr, s>>>(
                        d, B.nl, B.total_rows, cache, rt)));
       });
-      if (nlo) col_inv(d, nlo, smlo);
-      col_inv(d + nlo, B.nl - nlo, smc);
+      if (nlo) col_inv(d, nlo, smlo, B.clog_lo);
+      col_inv(d + nlo, B.nl - nlo, smc, B.clog);
     }
     if (B.ns) side.join();
     return cudaGetLastError();

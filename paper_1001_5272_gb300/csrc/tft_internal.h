@@ -80,6 +80,7 @@ struct BatchLaunch {
   uint32_t nl;
   int lr;              // row length of the large class
   int clog;            // columns per tile
+  int clog_lo;         // columns per tile of the shorter-column class
   int cmax;            // largest column log length
   uint32_t nl_lo;      // large products (first, sorted by c) with c < cmax
   int cmax_lo;         // their largest column log length

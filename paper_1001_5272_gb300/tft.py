@@ -44,7 +44,8 @@ class TransformDesc(ctypes.Structure):
 class BatchParams(ctypes.Structure):
     """tft_batch_params: 0 in a field selects the library default."""
     _fields_ = [("small_log", ctypes.c_uint32), ("lr", ctypes.c_uint32),
-                ("clog_plus1", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("clog_plus1", ctypes.c_uint32),
+                ("clog_lo_plus1", ctypes.c_uint32)]
 
 
 class Request(ctypes.Structure):
@@ -544,6 +545,8 @@ def _params(params):
     p.lr = int(params.get("lr", 0))
     clog = params.get("clog")
     p.clog_plus1 = 0 if clog is None else int(clog) + 1
+    clog_lo = params.get("clog_lo")
+    p.clog_lo_plus1 = 0 if clog_lo is None else int(clog_lo) + 1
     return ctypes.byref(p)
 
 

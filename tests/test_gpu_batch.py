@@ -111,7 +111,11 @@ def test_batch_mixed_classes(ctxs, pr):
     {"lr": 11, "small_log": 11, "clog": 1},
     {"lr": 12, "small_log": 12, "clog": 4},
     {"lr": 8, "small_log": 12, "clog": 5},
-], ids=lambda d: "lr{lr}-s{small_log}-c{clog}".format(**d))
+    {"lr": 8, "small_log": 9, "clog": 3, "clog_lo": 5},
+    {"lr": 9, "small_log": 9, "clog": 4, "clog_lo": 1},
+    {"lr": 10, "small_log": 10, "clog": 2, "clog_lo": 0},
+], ids=lambda d: "lr{lr}-s{small_log}-c{clog}-clo{}".format(
+    d.get("clog_lo", "-"), **d))
 def test_batch_schedules(ctxs, pr, params):
     pairs = [(300, 200), (256, 1), (257, 1), (1000, 3000), (4096, 4097),
              (9000, 7001), (30000, 40000), (2, 70000), (12345, 12345)]
@@ -313,7 +317,8 @@ def test_batch_argument_errors(ctxs):
         # schedule out of range (row length below 2^8; small class above
         # the shared-memory bound; small class below the row length)
         for bad in ({"lr": 7}, {"lr": 13}, {"small_log": 13},
-                    {"lr": 11, "small_log": 10}, {"clog": 6}):
+                    {"lr": 11, "small_log": 10}, {"clog": 6},
+                    {"clog_lo": 6}):
             with pytest.raises(tft.TFTError) as e:
                 tft.tft_batch_plan(ctx, [(a, b, out)], bad)
             assert e.value.status == tft.TFT_EINVAL, bad
