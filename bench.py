@@ -684,6 +684,37 @@ def run_ours(args):
                                          3 * bf_r + R_PROD,
                                          (NA + NB + R_PROD) * 4, 1)}
             del a32, b32, o32
+        # ---- the 500 x 500 product over 998244353 (launch-latency bound) -
+        from workloads import config1_inputs
+        ca, cb, cx = config1_inputs()
+        with tft.Context(0, dev, max_len=1 << 12) as c1:
+            ta1 = torch.from_numpy(ca.view(np.int32).copy()).to(dev)
+            tb1 = torch.from_numpy(cb.view(np.int32).copy()).to(dev)
+            tx1 = torch.from_numpy(cx.view(np.int32).copy()).to(dev)
+            o1 = torch.empty(999, dtype=torch.int32, device=dev)
+            res1 = {}
+            for name, fn in (
+                    ("polymul_us", lambda: tft.tft_polymul(c1, ta1, tb1, o1,
+                                                           stream)),
+                    ("forward_1000_us", lambda: tft.tft_forward(c1, tx1, 10,
+                                                                stream)),
+                    ("inverse_1000_us", lambda: tft.tft_inverse(c1, tx1, 10,
+                                                                stream))):
+                for _ in range(20):
+                    fn()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(200):
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                res1[name] = e0.elapsed_time(e1) * 1e3 / 200
+            res1["one_launch_each"] = True
+            res1["how"] = ("200 back-to-back calls on one stream, CUDA "
+                           "events around them; one single-CTA kernel per "
+                           "call")
+            extra["polymul_p998244353_500x500"] = res1
         # ---- end to end through the host-buffer entry point --------------
         out_pin = torch.empty(R_PROD, dtype=torch.int64).pin_memory()
         for _ in range(2):
