@@ -190,7 +190,8 @@ k_col_inv_batch(const BatchLarge* __restrict__ d, uint32_t nl,
     const BatchLarge q = d[p];
     const uint32_t j = (uint32_t)(task & ((1u << (lr - clog)) - 1));
     const uint64_t r = (uint64_t)q.A * R + q.Bm;
-    col_inv_tile<F>(smem_raw, s_rt, reinterpret_cast<T*>(q.out), nullptr, lr,
+    col_inv_tile<F, false>(smem_raw, s_rt, reinterpret_cast<T*>(q.out),
+                           nullptr, lr,
                     q.A + (q.Bm > 0 ? 1u : 0u), (int)q.c, clog, j * C, R, 0,
                     T(0), lr, r, reinterpret_cast<const T*>(q.EA));
   }

@@ -312,7 +312,7 @@ __device__ __forceinline__ void col_inv_stage_flat(
 // row pass leaves its inverse unscaled), removed here with the blocks' own
 // factors.
 // ---------------------------------------------------------------------------
-template <class F>
+template <class F, bool ASYNC_LOAD = true>
 __device__ void col_inv_tile(unsigned char* smem_raw,
                              const RootTable<typename F::T>& s_rt,
                              typename F::T* X, typename F::T* E, int lr,
@@ -362,25 +362,44 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
         s_thd[l] = th;
     }
   }
-  // 8 independent loads in flight per thread
+  // the tile; positions outside the columns or past m are zero.
+  // ASYNC_LOAD: asynchronous copies (every load of the thread in flight at
+  // once, no registers held; measured faster for the single transforms);
+  // otherwise eight loads in flight per thread through registers (measured
+  // faster for the batched products' short columns)
   const uint32_t nld = N << clog;
-#pragma unroll 1
-  for (uint32_t i0 = threadIdx.x; i0 < nld; i0 += 8 * blockDim.x) {
-    T v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t i = i0 + k * blockDim.x;
+  if constexpr (ASYNC_LOAD) {
+#pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < nld; i += blockDim.x) {
       const uint32_t t = i >> clog, cc = i & (C - 1);
       const uint64_t q = (uint64_t)q0 + cc;
       const uint64_t pos = q + (uint64_t)t * R;
-      v[k] = (i < nld && q < q_end && t < m)
-                 ? (pos < split ? X[pos] : Ealt[q])
-                 : T(0);
+      T* z = Z + (tswz(t, clog) << clog) + cc;
+      if (q < q_end && t < m)
+        cp_async_elem(z, pos < split ? X + pos : Ealt + q);
+      else
+        *z = T(0);
     }
+    cp_async_wait_all();
+  } else {
+#pragma unroll 1
+    for (uint32_t i0 = threadIdx.x; i0 < nld; i0 += 8 * blockDim.x) {
+      T v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t i = i0 + k * blockDim.x;
-      if (i < nld) Z[(tswz(i >> clog, clog) << clog) + (i & (C - 1))] = v[k];
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t i = i0 + k * blockDim.x;
+        const uint32_t t = i >> clog, cc = i & (C - 1);
+        const uint64_t q = (uint64_t)q0 + cc;
+        const uint64_t pos = q + (uint64_t)t * R;
+        v[k] = (i < nld && q < q_end && t < m)
+                   ? (pos < split ? X[pos] : Ealt[q])
+                   : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t i = i0 + k * blockDim.x;
+        if (i < nld) Z[(tswz(i >> clog, clog) << clog) + (i & (C - 1))] = v[k];
+      }
     }
   }
   __syncthreads();

@@ -295,17 +295,9 @@ k_row_inv2(typename F::T* X, uint64_t a, uint64_t rho_off,
     T* Grow = X + rho * R;
     if (active) {
       row_factors<F>(S, sp, LR, g, t, rho_off + rho, s_rt);
-      // eight loads in flight per thread
-      constexpr uint32_t NQ = R / Tpr;
-      static_assert(NQ % 8 == 0, "row load batches of eight");
-#pragma unroll
-      for (uint32_t k0 = 0; k0 < NQ; k0 += 8) {
-        T v[8];
-#pragma unroll
-        for (uint32_t k = 0; k < 8; ++k) v[k] = Grow[t + (k0 + k) * Tpr];
-#pragma unroll
-        for (uint32_t k = 0; k < 8; ++k) Zrow[swz(t + (k0 + k) * Tpr)] = v[k];
-      }
+      // asynchronous copies: all of the thread's positions in flight
+      for (uint32_t q = t; q < R; q += Tpr) cp_async_elem(Zrow + swz(q), Grow + q);
+      cp_async_wait_all();
     }
     __syncthreads();
 #pragma unroll 1
@@ -364,42 +356,16 @@ __device__ __forceinline__ void row_mul_body(
   }
   // both rows to shared memory (coalesced), then the first stage from
   // there: reading the first stage straight from global memory lets the
-  // scheduler overlap the two operands' loads and spill registers.  32-bit
-  // elements: eight positions of each operand in flight per thread (measured
-  // faster there, and slower for 64-bit elements, whose registers are
-  // scarcer)
-  if (active && sizeof(T) == 8) {
-    if (bsplit >= R) {
-      for (uint32_t q = t; q < R; q += Tpr) {
-        ZA[swz(q)] = GA[q];
-        ZB[swz(q)] = GB[q];
-      }
-    } else {
-      for (uint32_t q = t; q < R; q += Tpr) {
-        ZA[swz(q)] = q < bsplit ? GA[q] : EAg[q];
-        ZB[swz(q)] = q < bsplit ? GB[q] : EBg[q];
-      }
+  // scheduler overlap the two operands' loads and spill registers.  The
+  // loads are asynchronous copies straight into the swizzled rows, all of a
+  // thread's in flight at once without holding registers.
+  if (active) {
+    for (uint32_t q = t; q < R; q += Tpr) {
+      const bool mem = q < bsplit;  // bsplit >= R for a full row
+      cp_async_elem(ZA + swz(q), mem ? GA + q : EAg + q);
+      cp_async_elem(ZB + swz(q), mem ? GB + q : EBg + q);
     }
-  } else if (active) {
-    constexpr uint32_t NQ = R / Tpr;  // positions per thread
-    static_assert(NQ % 8 == 0, "row load batches of eight");
-#pragma unroll
-    for (uint32_t k0 = 0; k0 < NQ; k0 += 8) {
-      T va[8], vb[8];
-#pragma unroll
-      for (uint32_t k = 0; k < 8; ++k) {
-        const uint32_t q = t + (k0 + k) * Tpr;
-        const bool mem = q < bsplit;  // bsplit >= R for a full row
-        va[k] = mem ? GA[q] : EAg[q];
-        vb[k] = mem ? GB[q] : EBg[q];
-      }
-#pragma unroll
-      for (uint32_t k = 0; k < 8; ++k) {
-        const uint32_t q = t + (k0 + k) * Tpr;
-        ZA[swz(q)] = va[k];
-        ZB[swz(q)] = vb[k];
-      }
-    }
+    cp_async_wait_all();
   }
   __syncthreads();
   if (active) {

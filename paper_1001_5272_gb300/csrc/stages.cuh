@@ -36,6 +36,27 @@ __device__ __forceinline__ uint32_t swz(uint32_t p) {
   return p ^ ((p >> 4) & 15u);
 }
 
+// One element from global to shared memory by an asynchronous copy
+// (cp.async, 4 or 8 bytes): the load holds no register and a thread can
+// have all of its copies in flight; cp_async_wait_all() waits for the
+// thread's own copies (a barrier then publishes them to the CTA).
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* dst_smem, const T* src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d),
+                 "l"(src)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // Stage descriptor: levels [r_lo, r_lo + L).
 struct StageDesc {
   int r_lo;
