@@ -311,8 +311,14 @@ __device__ __forceinline__ void col_inv_stage_flat(
 // zero).  The tile's inputs may carry a factor 2^in_scale_log (the product's
 // row pass leaves its inverse unscaled), removed here with the blocks' own
 // factors.
+//
+// LASTROW: the tile is the ragged last row instead, one "column" of 2^c
+// contiguous words (lr = 0, clog = 0, m = b) that is block gblk = a of the
+// length-2^k network: every butterfly's twiddle takes the block's global
+// index ((gblk << c) + offset) >> level, and the known inputs at t >= m are
+// Ealt[t] (the short columns' E_t) instead of zero.
 // ---------------------------------------------------------------------------
-template <class F, bool ASYNC_LOAD = true>
+template <class F, bool ASYNC_LOAD = true, bool LASTROW = false>
 __device__ void col_inv_tile(unsigned char* smem_raw,
                              const RootTable<typename F::T>& s_rt,
                              typename F::T* X, typename F::T* E, int lr,
@@ -320,7 +326,8 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
                              uint32_t q_end, int want_E,
                              typename F::T omega_a_tw, int in_scale_log,
                              uint64_t split = ~0ull,
-                             const typename F::T* Ealt = nullptr) {
+                             const typename F::T* Ealt = nullptr,
+                             uint64_t gblk = 0) {
   using T = typename F::T;
   __syncthreads();  // the previous tile is done with shared memory
   // stage tables for 4-level stages: TL16[m'] = omega_{16 m'}, m' < 2^{c-4}
@@ -355,7 +362,13 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
     if (l >= 1 && l <= c) {
       const uint32_t low = m & ((1u << l) - 1);
       const bool up = asc && low >= (1u << (l - 1));
-      const T th = col_theta<F>(m >> l, s_rt, up);
+      T th;
+      if constexpr (LASTROW) {
+        th = row_factor<F>((gblk << (c - l)) + (m >> l), 1, s_rt, up);
+        if (up) th = F::mul_tw(th, s_rt.half_tw);
+      } else {
+        th = col_theta<F>(m >> l, s_rt, up);
+      }
       if (asc)
         s_tha[l] = th;
       else
@@ -368,7 +381,12 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
   // otherwise eight loads in flight per thread through registers (measured
   // faster for the batched products' short columns)
   const uint32_t nld = N << clog;
-  if constexpr (ASYNC_LOAD) {
+  if constexpr (LASTROW) {
+#pragma unroll 4
+    for (uint32_t t = threadIdx.x; t < N; t += blockDim.x)
+      cp_async_elem(Z + tswz(t, 0), t < m ? X + t : Ealt + t);
+    cp_async_wait_all();
+  } else if constexpr (ASYNC_LOAD) {
 #pragma unroll 4
     for (uint32_t i = threadIdx.x; i < nld; i += blockDim.x) {
       const uint32_t t = i >> clog, cc = i & (C - 1);
@@ -437,9 +455,12 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
     if (jj == nst)
       s_bsc[i] = pow2_inv<F>(k + in_scale_log, s_rt);
     else
-      s_rfi[jj * 14 + i] = k > 4 * jj ? row_factor<F>(s_boff[i] >> k,
-                                                      k - 4 * jj, s_rt, true)
-                                      : s_rt.one_tw;
+      s_rfi[jj * 14 + i] =
+          k > 4 * jj
+              ? row_factor<F>(LASTROW ? ((gblk << c) + s_boff[i]) >> k
+                                      : (uint64_t)(s_boff[i] >> k),
+                              k - 4 * jj, s_rt, true)
+              : s_rt.one_tw;
   }
   // an odd m leaves a block of one entry (row m - 1), which has no network
   // but still carries the inputs' scale
@@ -570,6 +591,22 @@ k_col_inv2(typename F::T* X, typename F::T* __restrict__ E, int lr,
   col_inv_tile<F>(smem_raw, s_rt, X, E, lr, m, c, clog,
                   q_begin + blockIdx.x * (1u << clog), q_end, want_E,
                   omega_a_tw, in_scale_log, split, Ealt);
+}
+
+// Inverse of the ragged last row (one CTA): block a of the network, outputs
+// known at q < b (in row) and inputs at q >= b (E_q = C_q(omega_a)); writes
+// the b recovered inputs (the long columns' last transform values) over the
+// outputs.  The generalized block inverse of the column tiles on one
+// contiguous 2^lr-word column whose twiddles carry the row index a.
+template <class F>
+__global__ void __launch_bounds__(512)
+k_lastrow_inv2(typename F::T* row, const typename F::T* __restrict__ E,
+               int lr, uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ RootTable<typename F::T> s_rt;
+  stage_roots<F>(&s_rt, rt);
+  col_inv_tile<F, true, true>(smem_raw, s_rt, row, nullptr, 0, (uint32_t)b,
+                              lr, 0, 0, 1, 0, s_rt.one_tw, 0, ~0ull, E, a);
 }
 
 }  // namespace tftgb

@@ -173,32 +173,6 @@ k_row_inv(typename F::T* X, int lr, uint64_t a, RootTable<typename F::T> rt) {
   }
 }
 
-// Last row inverse (one CTA): block a of the network with outputs known at
-// q < b and inputs known at q >= b (E_q = C_q(omega_a)).  Writes the b
-// recovered inputs (the long columns' last transform values).
-template <class F>
-__global__ void __launch_bounds__(512)
-k_lastrow_inv(typename F::T* row, const typename F::T* __restrict__ E, int lr,
-              uint64_t a, uint64_t b, RootTable<typename F::T> rt) {
-  using T = typename F::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ RootTable<T> s_rt;
-  load_roots<F>(&s_rt, rt);
-  const uint32_t R = 1u << lr;
-  T* Z = reinterpret_cast<T*>(smem_raw);
-  T* W = Z + R;
-  T* Wih = W + R / 2;
-  T* L = Wih + R / 2;
-  build_base_tables<F>(W, Wih, lr, s_rt);
-  for (uint32_t q = threadIdx.x; q < R; q += blockDim.x)
-    Z[q] = q < b ? row[q] : E[q];
-  __syncthreads();
-  RowTw<F> tw{W, Wih, L, &s_rt, a, lr};
-  inv_block<F>(Z, 0, 0, lr, (uint32_t)b, tw);
-  for (uint32_t q = threadIdx.x; q < b; q += blockDim.x)
-    row[q] = F::canon(Z[q]);
-}
-
 // ---------------------------------------------------------------------------
 // Fused product row pass, persistent over rows.  For a full row rho < a the
 // two column-transformed operands (A' in out, B' in work) are interleaved as
@@ -372,7 +346,7 @@ struct Launch {
     if ((e = set_smem<F>((const void*)k_row_fwd<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_row_inv<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_row_mul<F>, mx))) return e;
-    if ((e = set_smem<F>((const void*)k_lastrow_inv<F>, mx))) return e;
+    if ((e = set_smem<F>((const void*)k_lastrow_inv2<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_lastrow_cluster<F, false>, mx)))
       return e;
     if ((e = set_smem<F>((const void*)k_lastrow_cluster<F, true>, mx)))
@@ -547,7 +521,7 @@ struct Launch {
     }
     if (P.b > 0) {
       TFT_LAUNCH(K_LASTROW_INV,
-                 k_lastrow_inv<F><<<1, 512, smem_row<F>(P.lr, 1), s>>>(
+                 k_lastrow_inv2<F><<<1, 512, col_smem_bytes<T>(P.lr, 0), s>>>(
                      x + P.a * (uint64_t)R, E, P.lr, P.a, P.b, rt));
       const uint32_t qe = (uint32_t)P.b;
       const int cl = set_clog(P, qe, nsm);
@@ -675,7 +649,7 @@ struct Launch {
       });
     } else {
       TFT_LAUNCH(K_LASTROW_INV,
-                 k_lastrow_inv<F><<<1, 512, smem_row<F>(lr, 1), s>>>(
+                 k_lastrow_inv2<F><<<1, 512, col_smem_bytes<T>(lr, 0), s>>>(
                      row, E, lr, a, b, rt));
     }
     return cudaGetLastError();
