@@ -239,13 +239,16 @@ __device__ __forceinline__ typename F::T col_theta(
 // column's network, so the stage twist is omega_{(off >> k) 2^{k - r_lo}} *
 // omega_{B_local 2^L} (inverted here, RFi is the first factor's inverse).
 // The stage returns 2^L times its exact inverse (cnet_inv2); the stage that
-// reaches the block's top level (top) multiplies by sc, the block's whole
-// factor 2^-k (times any scale its inputs carry).
+// reaches the block's top level (top) also carries the block's whole factor
+// 2^-k (times any scale its inputs carry).  At the top stage B_local = 0 for
+// every unit of the block, so its twist and scale are one per-block table,
+// top_tab[i] = 2^-k RFi^i, instead of the powers of zeta per unit.
 template <class F, int L>
 __device__ __forceinline__ void col_inv_unit(
     typename F::T* Z, int clog, uint32_t off, int r_lo, uint32_t u,
     typename F::T RFi, const typename F::T* TL16i,
-    const StageConsts<typename F::T>& K, bool top, typename F::T sc) {
+    const StageConsts<typename F::T>& K, bool top,
+    const typename F::T* top_tab) {
   using T = typename F::T;
   constexpr int U = 1 << L;
   const uint32_t cc = u & ((1u << clog) - 1);
@@ -257,12 +260,13 @@ __device__ __forceinline__ void col_inv_unit(
     x[i] = Z[(tswz(t, clog) << clog) + cc];
   }
   cnet_inv2<F, L>(x, K);
-  // only the 4-level stages below a block's top have B_local != 0
-  const uint32_t bl = ut >> r_lo;
-  twist<F, L>(x, L == 4 && bl ? F::mul_tw(RFi, TL16i[bl]) : RFi);
   if (top) {
 #pragma unroll
-    for (int i = 0; i < U; ++i) x[i] = F::mul_tw(x[i], sc);
+    for (int i = 0; i < U; ++i) x[i] = F::mul_tw(x[i], top_tab[i]);
+  } else {
+    // only the 4-level stages below a block's top have B_local != 0
+    const uint32_t bl = ut >> r_lo;
+    twist<F, L>(x, L == 4 && bl ? F::mul_tw(RFi, TL16i[bl]) : RFi);
   }
 #pragma unroll
   for (int i = 0; i < U; ++i) {
@@ -276,7 +280,7 @@ __device__ __forceinline__ void col_inv_unit(
 template <class F, int L>
 __device__ __forceinline__ void col_inv_stage_flat(
     typename F::T* Z, int clog, int r_lo, int j, int nb, const int* bk,
-    const uint32_t* boff, const typename F::T* rfi, const typename F::T* bsc,
+    const uint32_t* boff, const typename F::T* rfi, const typename F::T* ttab,
     const typename F::T* TL16i, const StageConsts<typename F::T>& K) {
   uint32_t total = 0;
   for (int i = 0; i < nb; ++i) {
@@ -295,7 +299,7 @@ __device__ __forceinline__ void col_inv_stage_flat(
       u -= cnt;
     }
     col_inv_unit<F, L>(Z, clog, boff[i], r_lo, u, rfi[j * 14 + i], TL16i, K,
-                       bk[i] - r_lo == L, bsc[i]);
+                       bk[i] - r_lo == L, ttab + 16 * i);
   }
 }
 
@@ -431,6 +435,7 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
   __shared__ uint32_t s_boff[14];
   __shared__ T s_rfi[4 * 14];
   __shared__ T s_bsc[14];
+  __shared__ T s_ttab[14 * 16];
   __shared__ int s_nb;
   if (threadIdx.x == 0) {
     int nb = 0;
@@ -469,16 +474,28 @@ __device__ void col_inv_tile(unsigned char* smem_raw,
     *z = F::mul_tw(*z, pow2_inv<F>(in_scale_log, s_rt));
   }
   __syncthreads();
+  // each block's top-stage table: 2^-(k + in) RFi^t, t < 16, with RFi the
+  // row factor of the block's top stage (stage (k - 1) / 4)
+  for (int e = threadIdx.x; e < 16 * nb; e += blockDim.x) {
+    const int i = e >> 4;
+    T z = s_rfi[((s_bk[i] - 1) >> 2) * 14 + i], v = s_bsc[i];
+    for (int t = e & 15; t; t >>= 1) {
+      if (t & 1) v = F::mul_tw(v, z);
+      z = F::mul_tw(z, z);
+    }
+    s_ttab[e] = v;
+  }
+  __syncthreads();
   for (int jj = 0; jj < nst; ++jj) {
     const int r_lo = 4 * jj;
     col_inv_stage_flat<F, 4>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
-                             s_bsc, TL16i, *S.K);
+                             s_ttab, TL16i, *S.K);
     col_inv_stage_flat<F, 3>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
-                             s_bsc, TL16i, *S.K);
+                             s_ttab, TL16i, *S.K);
     col_inv_stage_flat<F, 2>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
-                             s_bsc, TL16i, *S.K);
+                             s_ttab, TL16i, *S.K);
     col_inv_stage_flat<F, 1>(Z, clog, r_lo, jj, nb, s_bk, s_boff, s_rfi,
-                             s_bsc, TL16i, *S.K);
+                             s_ttab, TL16i, *S.K);
     __syncthreads();
   }
   // ---- descent and ascent (one level each) -------------------------------
