@@ -118,8 +118,8 @@ k_col_fwd_batch(const BatchLarge* __restrict__ d, uint32_t nl, int lr,
     const T* src = reinterpret_cast<const T*>(o ? q.b : q.a);
     T* dst = reinterpret_cast<T*>(o ? q.work : q.out);
     T* E = reinterpret_cast<T*>(o ? q.EB : q.EA);
-    col_fwd_tile<F>(smem_raw, s_rt, src, o ? q.nb : q.na, dst, E, lr, q.A,
-                    q.Bm, (int)q.c, clog, j << clog, R);
+    col_fwd_tile<F, true>(smem_raw, s_rt, src, o ? q.nb : q.na, dst, E, lr,
+                          q.A, q.Bm, (int)q.c, clog, j << clog, R);
   }
 }
 

@@ -65,13 +65,16 @@ __host__ __device__ inline size_t col_smem_bytes(int c, int clog) {
 // to global memory (rows t < a to dst, row a to dst or E).  TZ (first stage
 // only): the operand has no entries in the upper half of the padded column
 // (rows >= 2^{c-1}), so the stage's top level is a copy and those inputs are
-// not loaded.
-template <class F, int L, bool FIRST, bool LAST, bool TZ = false>
+// not loaded.  PWT: the stage's twist powers come from PW by block,
+// PW[16 B + i] = TLs[B]^i, shared by the 16 C units of each block.
+template <class F, int L, bool FIRST, bool LAST, bool TZ = false,
+          bool PWT = false>
 __device__ __forceinline__ void col_fwd_stage(
     typename F::T* Z, const typename F::T* src, uint64_t n_src,
     typename F::T* dst, typename F::T* E, uint64_t R, uint64_t a, uint64_t b,
     uint32_t rows, int c, int clog, uint32_t q0, uint32_t q_end, int r_lo,
-    const typename F::T* TLs, const StageConsts<typename F::T>& K) {
+    const typename F::T* TLs, const StageConsts<typename F::T>& K,
+    const typename F::T* PW = nullptr) {
   using T = typename F::T;
   constexpr int U = 1 << L;
   const uint32_t C = 1u << clog;
@@ -106,7 +109,15 @@ __device__ __forceinline__ void col_fwd_stage(
     const uint64_t q = (uint64_t)q0 + cc;
     const bool colok = q < q_end;
     // the first stage's block index is 0: zeta = 1, no twist
-    if (!FIRST) twist<F, L>(x, TLs[ut >> r_lo]);
+    if (!FIRST) {
+      if constexpr (PWT) {
+        const T* pw = PW + 16 * (ut >> r_lo);
+#pragma unroll
+        for (int i = 1; i < U; ++i) x[i] = F::mul_tw(x[i], pw[i]);
+      } else {
+        twist<F, L>(x, TLs[ut >> r_lo]);
+      }
+    }
     cnet_fwd<F, L, FIRST && TZ>(x, K);
 #pragma unroll
     for (int i = 0; i < U; ++i) {
@@ -142,7 +153,7 @@ __device__ __forceinline__ void col_fwd_stage(
 // writes straight to global memory: rows t < a to dst, row a to dst for long
 // columns (q < b) and to E for short ones.
 // ---------------------------------------------------------------------------
-template <class F>
+template <class F, bool PWTAB = false>
 __device__ void col_fwd_tile(unsigned char* smem_raw,
                              const RootTable<typename F::T>& s_rt,
                              const typename F::T* src, uint64_t n_src,
@@ -156,6 +167,27 @@ __device__ void col_fwd_tile(unsigned char* smem_raw,
   fill_stage_consts<F>(S.K, s_rt, c);
   build_stage_tables<F>(S.TL, S.TLi, sp, c, s_rt);
   __syncthreads();
+  // PWTAB: the second stage's twist powers by block when it has at most 32
+  // blocks (the later stages have too many blocks for a table).  Each table
+  // row serves the 16 C units of its block, so it pays on wide tiles (the
+  // batched products' 32-column tiles: forward columns 4% faster); on the
+  // single transforms' 2- and 4-column tiles it measured slower.
+  __shared__ T s_pw[PWTAB ? 32 * 16 : 1];
+  const bool pw1 =
+      PWTAB && sp.n >= 2 && (c - sp.s[1].r_lo - sp.s[1].L) <= 5;
+  if (pw1) {
+    const T* TL1 = S.TL + sp.s[1].tl_off;
+    const int cnt = 16 << (c - sp.s[1].r_lo - sp.s[1].L);
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+      T z = TL1[e >> 4], v = s_rt.one_tw;
+      for (int t = e & 15; t; t >>= 1) {
+        if (t & 1) v = F::mul_tw(v, z);
+        z = F::mul_tw(z, z);
+      }
+      s_pw[e] = v;
+    }
+    __syncthreads();
+  }
   const uint64_t R = 1ull << lr;
   const uint32_t rows = (uint32_t)(a + (b > 0 ? 1 : 0));
   // the operand's rows (the longest column's) all below 2^{c-1}: the top
@@ -165,27 +197,36 @@ __device__ void col_fwd_tile(unsigned char* smem_raw,
     const int r_lo = sp.s[si].r_lo;
     const T* TLs = S.TL + sp.s[si].tl_off;
     const bool first = si == 0, last = si == sp.n - 1;
-#define TFT_COL_FWD_CALL(FI, LA, TZ)                                        \
+#define TFT_COL_FWD_CALL(FI, LA, TZ, PWT)                                   \
   TFT_STAGE_SWITCH(sp.s[si].L,                                              \
-                   (col_fwd_stage<F, LL, FI, LA, TZ>(                       \
+                   (col_fwd_stage<F, LL, FI, LA, TZ, PWT>(                  \
                        S.Z, src, n_src, dst, E, R, a, b, rows, c, clog, q0, \
-                       q_end, r_lo, TLs, *S.K)))
+                       q_end, r_lo, TLs, *S.K, s_pw)))
+    const bool pw = si == 1 && pw1;
     if (first && last) {
       if (tz) {
-        TFT_COL_FWD_CALL(true, true, true);
+        TFT_COL_FWD_CALL(true, true, true, false);
       } else {
-        TFT_COL_FWD_CALL(true, true, false);
+        TFT_COL_FWD_CALL(true, true, false, false);
       }
     } else if (first) {
       if (tz) {
-        TFT_COL_FWD_CALL(true, false, true);
+        TFT_COL_FWD_CALL(true, false, true, false);
       } else {
-        TFT_COL_FWD_CALL(true, false, false);
+        TFT_COL_FWD_CALL(true, false, false, false);
       }
     } else if (last) {
-      TFT_COL_FWD_CALL(false, true, false);
+      if (PWTAB && pw) {
+        TFT_COL_FWD_CALL(false, true, false, PWTAB);
+      } else {
+        TFT_COL_FWD_CALL(false, true, false, false);
+      }
     } else {
-      TFT_COL_FWD_CALL(false, false, false);
+      if (PWTAB && pw) {
+        TFT_COL_FWD_CALL(false, false, false, PWTAB);
+      } else {
+        TFT_COL_FWD_CALL(false, false, false, false);
+      }
     }
 #undef TFT_COL_FWD_CALL
     __syncthreads();
