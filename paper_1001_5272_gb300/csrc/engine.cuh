@@ -47,6 +47,9 @@ namespace tftgb {
 template <class F>
 struct ColTw {
   using T = typename F::T;
+  // no per-level table: consecutive levels that stay inside one warp's rows
+  // need only a warp barrier between them
+  static constexpr bool kWarpSync = true;
   const T* W;
   const T* Wih;
   __device__ __forceinline__ void prep_fwd(int, uint32_t) const {}
@@ -69,6 +72,7 @@ struct ColTw {
 template <class F>
 struct RowTw {
   using T = typename F::T;
+  static constexpr bool kWarpSync = false;  // prep_* rebuilds L per level
   const T* W;
   const T* Wih;
   T* L;                 // shared scratch of 2^{lr-1} entries
@@ -184,15 +188,25 @@ __device__ void fwd_pruned(typename F::T* Z, int clog, int slog, int l,
       *pu = F::add(u, m);
       *pw = F::sub(u, m);
     }
-    __syncthreads();
+    // A warp's pairs pi in [32 w, 32 w + 32) (+ multiples of the block)
+    // cover rows [64 w, 64 w + 64) >> clog of every column at each level r
+    // with 2^r <= 32 >> clog, so levels r and r - 1 then exchange data only
+    // inside the warp.
+    if (Tw::kWarpSync && r >= 1 && r <= 5 - clog)
+      __syncwarp();
+    else
+      __syncthreads();
   }
 }
 
 // Inverse butterflies of levels 0 .. top-1 on rows [0, lim_r) where lim_r is
 // given per level by the functor; used by inv_full (lim = 2^l) and phase A.
+// wsync: the next level (r + 1) stays inside each warp's rows (see
+// fwd_pruned), so a warp barrier ends this one.
 template <class F, class Tw>
 __device__ __forceinline__ void inv_level(typename F::T* Z, int clog, int slog,
-                                          int r, uint32_t lim, const Tw& tw) {
+                                          int r, uint32_t lim, const Tw& tw,
+                                          bool wsync = false) {
   using T = typename F::T;
   const uint32_t C = 1u << clog;
   tw.prep_inv(r, lim >> (r + 1));
@@ -209,13 +223,75 @@ __device__ __forceinline__ void inv_level(typename F::T* Z, int clog, int slog,
     *pu = F::half(F::add(X, Y));
     *pw = F::mul_tw(F::sub(X, Y), th);
   }
-  __syncthreads();
+  if (wsync)
+    __syncwarp();
+  else
+    __syncthreads();
 }
 
 template <class F, class Tw>
 __device__ void inv_full(typename F::T* Z, int clog, int slog, int l,
                          const Tw& tw) {
-  for (int r = 0; r < l; ++r) inv_level<F>(Z, clog, slog, r, 1u << l, tw);
+  for (int r = 0; r < l; ++r)
+    inv_level<F>(Z, clog, slog, r, 1u << l, tw,
+                 Tw::kWarpSync && r + 1 < l && r + 1 <= 5 - clog);
+}
+
+// Levels 1..5 of inv_block's descent and ascent for one column (clog = 0):
+// below level 6 both stay inside the 32-row block of m0 (rows base + lane,
+// base = m0 rounded down to a multiple of 32), so warp 0 runs them with one
+// row per lane and level l pairing lanes lane and lane ^ 2^(l-1) by
+// shuffles, with no barrier between levels; the operations are those of
+// inv_block's own levels.  Returns nothing; the caller's barrier follows.
+template <class F, class Tw>
+__device__ __forceinline__ void inv_block_low_warp(typename F::T* Z, int slog,
+                                                   uint32_t m0, const Tw& tw) {
+  using T = typename F::T;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t base = m0 & ~31u;
+  T* z = Z + ((size_t)(base + lane) << slog);
+  T x = *z;
+  int lstop = 0;
+#pragma unroll 1
+  for (int l = 5; l >= 1; --l) {
+    const uint32_t low = m0 & ((1u << l) - 1);
+    if (low == 0) {
+      lstop = l;
+      break;
+    }
+    const uint32_t B = m0 & ~((1u << l) - 1);
+    const uint32_t h = 1u << (l - 1);
+    const T th = tw.fwd_direct(l - 1, B >> l);
+    const bool upc = low >= h;
+    const uint32_t j0 = upc ? low - h : low;
+    const T y = __shfl_xor_sync(0xffffffffu, x, h);
+    const bool in = (lane & ~((1u << l) - 1)) == B - base &&
+                    (lane & (h - 1)) >= j0;
+    const bool upper = (lane & h) != 0;
+    if (in && upc && upper) {
+      const T t = F::mul_tw(x, th);
+      x = F::sub(F::sub(y, t), t);
+    } else if (in && !upc && !upper) {
+      x = F::add(x, F::mul_tw(y, th));
+    }
+  }
+#pragma unroll 1
+  for (int l = lstop + 1; l <= 5; ++l) {
+    const uint32_t low = m0 & ((1u << l) - 1);
+    const uint32_t B = m0 & ~((1u << l) - 1);
+    const uint32_t h = 1u << (l - 1);
+    const bool up = low >= h;
+    const T th = up ? tw.invh_direct(l - 1, B >> l) : tw.fwd_direct(l - 1, B >> l);
+    const T y = __shfl_xor_sync(0xffffffffu, x, h);
+    const bool in = (lane & ~((1u << l) - 1)) == B - base;
+    const bool upper = (lane & h) != 0;
+    if (in && up) {
+      x = upper ? F::mul_tw(F::sub(y, x), th) : F::half(F::add(x, y));
+    } else if (in && !upper) {
+      x = F::sub(x, F::mul_tw(y, th));
+    }
+  }
+  *z = x;
 }
 
 // Generalized inverse on the padded block of 2^l0 rows: rows < m0 hold known
@@ -236,15 +312,21 @@ __device__ void inv_block(typename F::T* Z, int clog, int slog, int l0,
   for (int r = 0; r < l0; ++r) {
     const uint32_t lim = (m0 >> (r + 1)) << (r + 1);
     if (lim == 0) break;  // lim is non-increasing in r
-    inv_level<F>(Z, clog, slog, r, lim, tw);
+    const bool next = r + 1 < l0 && (m0 >> (r + 2)) != 0;
+    inv_level<F>(Z, clog, slog, r, lim, tw,
+                 Tw::kWarpSync && next && r + 1 <= 5 - clog);
   }
   // Descent: levels l = l0 .. 1 while m0 mod 2^l != 0.  The block at level
   // l starts at row B = m0 with its low l bits cleared; m = m0 mod 2^l.
+  // With one column, levels 1..5 go to inv_block_low_warp.
+  const int wl = (clog == 0 && l0 >= 5) ? 5 : 0;
   int lstop = 0;
-  for (int l = l0; l >= 1; --l) {
+  bool stopped = false;
+  for (int l = l0; l > wl; --l) {
     const uint32_t low = m0 & ((1u << l) - 1);
     if (low == 0) {
       lstop = l;
+      stopped = true;
       break;
     }
     const uint32_t B = m0 & ~((1u << l) - 1);
@@ -274,6 +356,13 @@ __device__ void inv_block(typename F::T* Z, int clog, int slog, int l0,
       }
     }
     __syncthreads();
+  }
+  if (!stopped && wl > 0) {
+    if (m0 & 31u) {
+      if (threadIdx.x < 32) inv_block_low_warp<F>(Z, slog, m0, tw);
+      __syncthreads();
+    }
+    lstop = wl;
   }
   // Ascent: the same levels bottom-up.
   for (int l = lstop + 1; l <= l0; ++l) {
