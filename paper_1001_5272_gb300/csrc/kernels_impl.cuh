@@ -349,7 +349,10 @@ struct Launch {
     if ((e = set_smem<F>((const void*)k_lastrow_inv2<F>, mx))) return e;
     if ((e = set_smem<F>((const void*)k_lastrow_cluster<F, false>, mx)))
       return e;
-    if ((e = set_smem<F>((const void*)k_lastrow_cluster<F, true>, mx)))
+    if ((e = set_smem<F>(
+             (const void*)k_lastrow_cluster<typename ClusterField<F>::type,
+                                            true>,
+             mx)))
       return e;
     TFT_PREP_LR(8);
     TFT_PREP_LR(9);
@@ -678,7 +681,8 @@ struct Launch {
     const size_t sm = lastrow_cluster_smem<T>(P.lr, P.b);
     if (inv)
       TFT_LAUNCH(K_LASTROW_INV,
-                 (k_lastrow_cluster<F, true><<<kLastRowCluster, 512, sm, s>>>(
+                 (k_lastrow_cluster<typename ClusterField<F>::type, true>
+                  <<<kLastRowCluster, 512, sm, s>>>(
                      x, P.lr, P.a, P.b, omega_a_tw, rt)));
     else
       TFT_LAUNCH(K_LASTROW_FWD,
